@@ -1,0 +1,332 @@
+#!/usr/bin/env python
+"""Benchmark of the DZS TreePM step on GB300 (one JSON line on rank 0).
+
+Workload (default): a single 128^3-particle lightcone mock, L = 256 Mpc/h,
+PM mesh 256^3, FP32 forces, DZS on (merge level 3), Zel'dovich ICs at z = 49
+(seed 2, sigma8 = 0.8), 96 global KDK steps uniform in ln a to z = 0, observer
+at the box centre, R_lc sweeping the box once.  A "step" is one full KDK step
+(kick + drift + crossing + records, Morton sort, DZS merge, tree, PM, walk +
+closing kick).  W warm-up steps start from the ICs; the K timed steps continue
+the run (when the run reaches a = 1 it restarts from fresh ICs outside the
+timed region).  value = N_init x K / device time ("effective" particle-steps/s).
+
+--impl reference times the FP64 CPU oracle (the reference arm of this build)
+on the same metric, on a 32^3 sub-box with the same particle and mesh spacing.
+"""
+import argparse
+import json
+import os
+import shutil
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s DZS FP32 vs plain FP64 at stated force error; mocks/h, p99 lat"
+UNIT = "particle-steps/s"
+# nominal FP32 pipe: 152 SMs x 128 lanes x 2 flop (FMA) x 2.07 GHz max SM clock
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# arithmetic of one pair evaluation of the FP32 walk ("walk roofline")
+FLOP_PER_PAIR = 38
+
+C2 = dict(n1d=128, mesh=256, box=256.0, merge_level=3, seed=2, sigma8=0.8)
+
+
+def workload_params(dzs, precision):
+    return dzs.params(**C2, precision=precision)
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        smi = shutil.which("nvidia-smi")
+        if not smi:
+            return
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        self.proc = subprocess.Popen([smi, "-i", str(self.index), "--query-gpu=" + q, "--format=csv,noheader,nounits",
+                                      "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def cpu_baseline(steps_cap=96):
+    """The FP64 oracle, as it stands, on a 32^3 sub-box with the bench's particle
+    spacing (2 Mpc/h), mesh spacing (1 Mpc/h) and DZS parameters: a full run of
+    96 steps (about 10-30 s of host CPU work)."""
+    import oracle as O
+    P = O.params(n1d=32, mesh=64, box=64.0, merge_level=3, seed=2, sigma8=0.8)
+    st = O.initial_state(P)
+    t0 = time.perf_counter()
+    n = min(steps_cap, P.nsteps)
+    for s in range(n):
+        st, _ = O.step(P, s, st)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": 32 ** 3 * n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "full %d-step run of a 32^3-particle, 64 Mpc/h sub-box (mesh 64^3) with the bench's "
+                      "spacing and DZS parameters, FP64 oracle, %.1f s" % (n, dt)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
+    import oracle as O
+    P = O.params(n1d=32, mesh=64, box=64.0, merge_level=3, seed=2, sigma8=0.8)
+    st = O.initial_state(P)
+    step = 0
+    for _ in range(args.warmup):
+        if step == P.nsteps:
+            st, step = O.initial_state(P), 0
+        st, _ = O.step(P, step, st)
+        step += 1
+    total = 0.0
+    for _ in range(args.steps):
+        if step == P.nsteps:
+            st, step = O.initial_state(P), 0
+        t0 = time.perf_counter()
+        st, _ = O.step(P, step, st)
+        total += time.perf_counter() - t0
+        step += 1
+    v = 32 ** 3 * args.steps / total
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "FP64 CPU oracle, 32^3 particles in 64 Mpc/h (mesh 64^3), "
+                                                       "same spacing and DZS parameters as the 128^3 mock",
+                                            "parallelism": "host cores"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d oracle steps of the 32^3 sub-box" % args.steps},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=93)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import paper_2005_05328_gb300 as dzs
+    from paper_2005_05328_gb300 import build as libbuild
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if rank == 0:
+        libbuild.build()
+    if world > 1:
+        dist.barrier()
+    dzs.load()
+    stream = torch.cuda.Stream()
+    P = workload_params(dzs, dzs.FP32)
+    P.device = local
+    ctx = dzs.Context(P, stream=stream.cuda_stream)
+    n0 = P.n1d ** 3
+    nst = P.nsteps
+    with torch.cuda.stream(stream):
+        ctx.ics()
+        step = 0
+        for _ in range(args.warmup):
+            if step == nst:
+                ctx.ics()
+                step = 0
+            ctx.step(1)
+            step += 1
+        torch.cuda.synchronize()
+        sampler = ClockSampler(local)
+        sampler.start()
+        ctx.set_profiling(True)
+        l0 = int(ctx.counters()[4])
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        segs = []
+        ev_a = torch.cuda.Event(enable_timing=True)
+        ev_a.record(stream)
+        done = 0
+        relaunch = 0
+        while done < args.steps:
+            if step == nst:
+                ev_b = torch.cuda.Event(enable_timing=True)
+                ev_b.record(stream)
+                segs.append((ev_a, ev_b))
+                prof_keep = ctx.profile()
+                ctx.ics()
+                step = 0
+                for _ in range(args.warmup):
+                    ctx.step(1)
+                    step += 1
+                relaunch += 1
+                ev_a = torch.cuda.Event(enable_timing=True)
+                ev_a.record(stream)
+            ctx.step(1)
+            step += 1
+            done += 1
+        ev_b = torch.cuda.Event(enable_timing=True)
+        ev_b.record(stream)
+        segs.append((ev_a, ev_b))
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        clocks = sampler.stop()
+        ms = sum(a.elapsed_time(b) for a, b in segs)
+        prof = ctx.profile()
+        cnt = ctx.counters()
+        launches = int(cnt[4]) - l0
+        pairs = int(cnt[2])
+        n_final, _ = ctx.count()
+    t_local = ms / 1e3
+    if world > 1:
+        t = torch.tensor([t_local], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    else:
+        t_max = t_local
+    value = n0 * args.steps * world / t_max
+
+    # e2e through the public API with host buffers (rank 0 measures, others replicate)
+    e2e = None
+    if not args.no_e2e:
+        e2e = measure_e2e(dzs, P, stream, min(args.steps, nst))
+
+    if rank != 0:
+        return
+    # roofline of the dominant stage
+    pk = peaks()
+    dom = max(prof, key=lambda k: prof[k][0])
+    walk_ms, walk_calls = prof["walk"]
+    walk_avg_s = walk_ms / 1e3 / max(1, walk_calls)
+    achieved_tf = pairs / max(1, walk_calls) * FLOP_PER_PAIR / walk_avg_s / 1e12
+    roof = {"bound": "alu", "kernel": "k_walk<float> (tree walk + closing kick)", "achieved": achieved_tf,
+            "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved_tf / FP32_PEAK_TFLOPS, "traffic": None,
+            "peak_source": "nominal FP32 FMA rate 152 SM x 128 lanes x 2 x 2.07 GHz (no measured FP32 peak in "
+                           "MEASURED_PEAKS.json)",
+            "pairs_per_launch": pairs / max(1, walk_calls), "flop_per_pair": FLOP_PER_PAIR,
+            "avg_launch_ms": walk_avg_s * 1e3, "dominant_stage": dom}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "single lightcone mock: N=128^3, L=256 Mpc/h, mesh 256^3, FP32 forces (u32 lattice "
+                               "positions), DZS merge level 3, 96 KDK steps z=49->0, steps %d..%d timed"
+                               % (args.warmup, args.warmup + args.steps - 1),
+                   "global_batch": n0 * world, "parallelism": "replicas x%d" % world,
+                   "l2": "inputs larger than L2 (state + 256^3 mesh > 129 MB)", "restarts_in_timed_region": relaunch,
+                   "n_active_end": int(n_final)},
+        "roofline": roof,
+        "stage_ms": {k: v[0] for k, v in prof.items()},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "e2e": e2e,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        try:
+            line["cpu_baseline"] = cpu_baseline()
+        except Exception as ex:  # the oracle needs gcc; report why it is missing
+            line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                                    "sample": "unavailable: %s" % ex}
+    print(json.dumps(line), flush=True)
+
+
+def measure_e2e(dzs, P, stream, k):
+    """Same metric through the C ABI with host buffers: the IC state is copied
+    in from pinned host memory, then every step runs and its lightcone records
+    and diagnostics are copied back to the host."""
+    import torch
+    ctx = dzs.Context(P, stream=stream.cuda_stream)
+    with torch.cuda.stream(stream):
+        ctx.ics()
+        st = ctx.state()
+        n = st["u"].shape[1]
+        pinned = {}
+        for key, arr in st.items():
+            t = torch.empty(arr.shape, dtype={np.uint32: torch.int32, np.float64: torch.float64,
+                                              np.uint8: torch.uint8}[arr.dtype.type], pin_memory=True)
+            t.numpy().view(arr.dtype)[...] = arr
+            pinned[key] = t.numpy().view(arr.dtype)
+        h2d = sum(a.nbytes for a in pinned.values())
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.set_state(pinned, 0)
+        d2h = 0
+        for _ in range(k):
+            ctx.step(1)
+            rec = ctx.drain(cap=n)
+            d = ctx.diagnostics()
+            d2h += rec.nbytes + d.nbytes
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    ctx.close()
+    return {"value": P.n1d ** 3 * k / wall, "unit": UNIT, "h2d_bytes_per_step": h2d / k,
+            "d2h_bytes_per_step": d2h / k, "steps": k}
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,228 @@
+/*
+ * dzs.h -- C ABI of the GB300-native Dynamic Zoom Simulations TreePM step.
+ *
+ * Paper: Garaldi, Nori & Baldi, "Dynamic Zoom Simulations: a fast, adaptive
+ * algorithm for simulating lightcones", arXiv 2005.05328.
+ *
+ * Problem statement (paper Sec. 1 footnote and Sec. 2.2.1): given initial
+ * conditions, a cosmology, an observer at the box centre and the DZS
+ * parameters (theta_dzs, buffer b, maximum node size l_max), evolve the
+ * particles to z = 0 with TreePM gravity (Sec. 2.1), output every particle
+ * once as the lightcone R_lc(a) sweeps it (Sec. 3.1.3), and de-refine the
+ * particles outside R_lc + b by merging oct-tree nodes into centre-of-mass
+ * particles (Sec. 2.2, Eq. 3).
+ *
+ * Conventions of every entry point
+ *   - Positions are uint32 lattice coordinates u = floor(x / L * 2^32) per
+ *     axis, stored SoA: u[0..n) is x, u[n..2n) is y, u[2n..3n) is z.  The
+ *     observer sits at u = 2^31 on each axis.  Momenta p = a^2 dx/dt and
+ *     accelerations g are SoA [3][n] in Mpc/h units with H0 = 1, always
+ *     exchanged as double (converted on the device in DZS_FP32 mode).
+ *   - Masses are uint32 multiplicities k of the base mass m0
+ *     (4 pi G m0 = 1.5 Omega_m L^3 / N0, N0 = n1d^3).
+ *   - Host pointers are caller-owned host memory; the context owns all device
+ *     memory (one cudaMalloc'd arena per context) and its CUDA stream use.
+ *   - Every call returns a dzs_status; errors never abort the process.
+ *     DZS_EDEVICE / DZS_ETIMEOUT poison the context (only dzs_destroy is then
+ *     valid).  dzs_last_error() gives a message for the last failure.
+ *   - dzs_step enqueues on the context stream and returns; calls that return
+ *     host data (drain, get_state, diagnostics, accel, ...) synchronise it.
+ *   - One context is used by one host thread at a time.
+ */
+#ifndef DZS_H
+#define DZS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define DZS_API __attribute__((visibility("default")))
+#else
+#define DZS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dzs_ctx dzs_ctx;
+
+typedef enum {
+  DZS_OK = 0,
+  DZS_EINVAL = 1,    /* invalid argument or parameter set */
+  DZS_ENOMEM = 2,    /* device or host allocation failed */
+  DZS_ECUDA = 3,     /* a CUDA runtime call failed (message in dzs_last_error) */
+  DZS_EOVERFLOW = 4, /* a device buffer filled up (tree nodes, walk stack, lightcone ring) */
+  DZS_ETIMEOUT = 5,  /* a bounded device wait gave up */
+  DZS_ESTATE = 6,    /* call not valid in the context's current state */
+  DZS_EDEVICE = 7    /* no usable CUDA device / unsupported architecture */
+} dzs_status;
+
+enum { DZS_RLC_SWEEP = 0, DZS_RLC_PHYSICAL = 1 };
+enum { DZS_FP32 = 0, DZS_FP64 = 1 };
+
+/* flag bits of a particle */
+enum { DZS_FL_CROSSED = 1, DZS_FL_MERGED = 2 };
+
+/* stage bits for dzs_run_stages */
+enum {
+  DZS_STAGE_KICK_DRIFT = 1, /* opening kick, drift, crossing test, Morton keys, records */
+  DZS_STAGE_SORT = 2,       /* stable radix sort of the keys + state permutation */
+  DZS_STAGE_MERGE = 4,      /* DZS merge against R_lc(a_step+1) (only if dzs_on) */
+  DZS_STAGE_FORCE = 8,      /* tree build, PM, tree walk: g of the current particles */
+  DZS_STAGE_CLOSE = 16,     /* closing kick p += g K(a_step+1/2, a_step+1) */
+  DZS_STAGE_ALL = 31
+};
+
+/* parts for dzs_accel */
+enum { DZS_ACC_PM = 1, DZS_ACC_TREE = 2, DZS_ACC_ALL = 3 };
+
+/* mesh selectors for dzs_get_mesh */
+enum { DZS_MESH_DELTA = 0, DZS_MESH_PHI = 1 };
+
+typedef struct {
+  int32_t n1d;          /* particles per side at the start, N0 = n1d^3 (power of two, 8..512) */
+  int32_t mesh;         /* PM mesh points per side M (power of two, 16..512) */
+  double box;           /* L [Mpc/h] */
+  double omega_m, omega_l, hubble, sigma8, ns;
+  double z_init;        /* initial redshift (49) */
+  int32_t nsteps;       /* global KDK steps, uniform in ln a to a = 1 */
+  int32_t leaf_bucket;  /* B: leaf holds <= B particles (physics parameter) */
+  int32_t walk_group;   /* G: walk group size bound, 32 (physics parameter) */
+  int32_t dzs_on;       /* 1: DZS merge every step */
+  int32_t merge_level;  /* l_max = 2^(merge_level-1) * L / n1d */
+  int32_t rlc_mode;     /* DZS_RLC_SWEEP | DZS_RLC_PHYSICAL */
+  double rs_cells;      /* PM split scale r_s in mesh cells (1.25) */
+  double rcut_rs;       /* short-range cut r_cut / r_s (4.5) */
+  double theta;         /* force-walk opening angle, Eq. 1 (0.5) */
+  double soft_frac;     /* eps0 / (L / n1d) (1/40) */
+  double theta_dzs;     /* DZS geometric merge angle, Sec. 2.2.1 (0.1) */
+  double buffer_cells;  /* buffer b of Eq. 3 in mesh cells (2) */
+  uint64_t seed;        /* IC white-noise seed */
+  int32_t precision;    /* DZS_FP32 | DZS_FP64 force arithmetic */
+  int32_t device;       /* CUDA device ordinal */
+  uint64_t lc_capacity; /* lightcone ring records; 0 = N0 (never overflows) */
+} dzs_params;
+
+/* one lightcone record: particle id and multiplicity, crossing expansion
+ * factor a*, comoving position x* [Mpc/h] in [0, L) and momentum p (64 bytes) */
+typedef struct {
+  uint32_t id, k;
+  double a_cross;
+  double x[3];
+  double p[3];
+} dzs_lc_record;
+
+/* Fill *p with the configuration-1 defaults of the paper's method
+ * (32^3 particles in 64 Mpc/h, mesh 64, r_s = 1.25 cells, r_cut = 4.5 r_s,
+ * theta = 0.5, eps0 = lambda/40, DZS on, merge level 2, theta_dzs = 0.1,
+ * b = 2 cells, 96 steps from z = 49, FP32).  Returns DZS_EINVAL if p is NULL. */
+DZS_API dzs_status dzs_params_default(dzs_params* p);
+
+/* Device bytes a context with these parameters allocates (for admission by
+ * memory budget).  DZS_EINVAL on an invalid parameter set. */
+DZS_API dzs_status dzs_footprint_bytes(const dzs_params* p, size_t* bytes);
+
+/* Validate p, compute the FP64 host tables (time integrals, R_lc), allocate
+ * the device arena on p->device and bind cuda_stream (a cudaStream_t; NULL =
+ * the legacy default stream).  On success *out owns everything; the particle
+ * state is empty until dzs_ics or dzs_set_state. */
+DZS_API dzs_status dzs_create(const dzs_params* p, void* cuda_stream, dzs_ctx** out);
+
+/* Zel'dovich initial conditions at z_init from the seeded Gaussian field
+ * (paper Fig. 1 caption: linear theory to z ~ 50), initial lightcone flags
+ * (PHYSICAL mode), Morton sort and the first accelerations.  Step index 0. */
+DZS_API dzs_status dzs_ics(dzs_ctx* c);
+
+/* Enqueue up to nsteps full KDK steps (DZS_STAGE_ALL), stopping at a = 1.
+ * *steps_done (nullable) receives the number enqueued. */
+DZS_API dzs_status dzs_step(dzs_ctx* c, int32_t nsteps, int32_t* steps_done);
+
+/* Run the stages in stage_mask of the current step in stage order, without
+ * advancing the step index unless DZS_STAGE_CLOSE is included.  Used for
+ * per-stage parity tests and timing. */
+DZS_API dzs_status dzs_run_stages(dzs_ctx* c, uint32_t stage_mask);
+
+/* Copy the lightcone records written since the last drain (in step order,
+ * within a step in the particle order at crossing) into host_buf, at most cap
+ * of them; *n_out = number copied.  Remaining records stay for the next
+ * drain.  Returns DZS_EOVERFLOW if records were dropped because the ring was
+ * full (the count of kept records is still valid). */
+DZS_API dzs_status dzs_lightcone_drain(dzs_ctx* c, dzs_lc_record* host_buf, size_t cap, size_t* n_out);
+
+/* Free the context and its device memory.  NULL-safe. */
+DZS_API dzs_status dzs_destroy(dzs_ctx* c);
+
+/* Current particle count and step index (synchronises). */
+DZS_API dzs_status dzs_get_count(dzs_ctx* c, size_t* n, int32_t* step);
+
+/* Copy the state out (host arrays sized >= cap particles; SoA with stride n
+ * for u, p, g).  Any pointer may be NULL to skip it.  *n = particle count. */
+DZS_API dzs_status dzs_get_state(dzs_ctx* c, uint32_t* u, double* p, double* g, uint32_t* k,
+                         uint32_t* id, uint8_t* fl, size_t cap, size_t* n);
+
+/* Replace the state with n particles (n <= N0) at step index `step`.
+ * g may be NULL (accelerations are then computed: DZS_STAGE_FORCE).  The
+ * order is kept as given; dzs_run_stages(DZS_STAGE_SORT) sorts it. */
+DZS_API dzs_status dzs_set_state(dzs_ctx* c, const uint32_t* u, const double* p, const double* g,
+                         const uint32_t* k, const uint32_t* id, const uint8_t* fl, size_t n,
+                         int32_t step);
+
+/* Accelerations of the current particle set (PM and/or tree part), written
+ * to g_out [3][n] in the current particle order.  The state is not modified. */
+DZS_API dzs_status dzs_accel(dzs_ctx* c, int32_t parts, double* g_out);
+
+/* Run the DZS merge alone (paper Sec. 2.2) on the current state, which must
+ * be Morton-sorted, against the lattice lightcone radius rlat
+ * (R_lc / L * 2^32). */
+DZS_API dzs_status dzs_merge_only(dzs_ctx* c, uint64_t rlat);
+
+/* Sum k, Sum k p[3], Sum k x[3] (Mpc/h), N (FP64; integer sums exact). */
+DZS_API dzs_status dzs_diagnostics(dzs_ctx* c, double out[8]);
+
+/* The context's FP64 tables: a[nsteps+1], drift[nsteps], kick1[nsteps]
+ * (a_n -> a_n+1/2), kick2[nsteps] (a_n+1/2 -> a_n+1), rlc[nsteps+1] (Mpc/h),
+ * rlat[nsteps+1].  Any pointer may be NULL. */
+DZS_API dzs_status dzs_get_tables(dzs_ctx* c, double* a, double* drift, double* kick1, double* kick2,
+                          double* rlc, uint64_t* rlat);
+
+/* Copy the PM density contrast or potential of the last force evaluation
+ * ([M][M][M], iz fastest) as double. */
+DZS_API dzs_status dzs_get_mesh(dzs_ctx* c, int32_t which, double* out);
+
+/* Counters: [0] walk groups and [1] tree nodes of the last force evaluation,
+ * [2] pair evaluations (interaction-list entries x group particles) summed
+ * since the last dzs_ics / dzs_set_state / dzs_set_profiling, [3] device error
+ * word, [4] kernels launched by this context so far, [5] lightcone records
+ * written so far. */
+DZS_API dzs_status dzs_get_counters(dzs_ctx* c, uint64_t out[6]);
+
+/* profile categories of dzs_get_profile */
+enum {
+  DZS_PROF_KICK_DRIFT = 0, /* opening kick, drift, crossing, record compaction */
+  DZS_PROF_SORT = 1,       /* radix sort + permutation */
+  DZS_PROF_MERGE = 2,      /* DZS merge */
+  DZS_PROF_TREE = 3,       /* tree build + group list */
+  DZS_PROF_PM = 4,         /* CIC deposit, FFT Poisson solve, gradient + interpolation */
+  DZS_PROF_WALK = 5,       /* tree walk + closing kick */
+  DZS_PROF_N = 6
+};
+
+/* Enable (1) or disable (0) per-stage CUDA-event timing on the context
+ * stream and reset the accumulators and the pair counter.  Timing adds two
+ * event records per stage and no synchronisation. */
+DZS_API dzs_status dzs_set_profiling(dzs_ctx* c, int32_t enable);
+
+/* Device milliseconds and call counts per category since the last
+ * dzs_set_profiling (synchronises; either pointer may be NULL). */
+DZS_API dzs_status dzs_get_profile(dzs_ctx* c, double ms[DZS_PROF_N], uint64_t calls[DZS_PROF_N]);
+
+/* Message of the last failure on this context (valid until the next call).
+ * c may be NULL (then: the last dzs_create failure of this thread). */
+DZS_API const char* dzs_last_error(const dzs_ctx* c);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DZS_H */

@@ -1,0 +1,271 @@
+"""Thin Python binding of the DZS TreePM C ABI (include/dzs.h).
+
+Argument marshalling only: every step of the method runs in the CUDA kernels of
+libdzs.so (built for sm_103a by ``paper_2005_05328_gb300.build``).  There is no
+CPU fallback: if the library is missing or the device is not a GB300 the calls
+raise.  Function names match the C entry points (``dzs_create`` ...); the
+``Context`` class bundles them for convenience.
+
+Paper: Garaldi, Nori & Baldi, "Dynamic Zoom Simulations", arXiv 2005.05328.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdzs.so")
+
+DZS_OK, DZS_EINVAL, DZS_ENOMEM, DZS_ECUDA, DZS_EOVERFLOW, DZS_ETIMEOUT, DZS_ESTATE, DZS_EDEVICE = range(8)
+STATUS_NAMES = ["DZS_OK", "DZS_EINVAL", "DZS_ENOMEM", "DZS_ECUDA", "DZS_EOVERFLOW", "DZS_ETIMEOUT",
+                "DZS_ESTATE", "DZS_EDEVICE"]
+RLC_SWEEP, RLC_PHYSICAL = 0, 1
+FP32, FP64 = 0, 1
+FL_CROSSED, FL_MERGED = 1, 2
+STAGE_KICK_DRIFT, STAGE_SORT, STAGE_MERGE, STAGE_FORCE, STAGE_CLOSE, STAGE_ALL = 1, 2, 4, 8, 16, 31
+ACC_PM, ACC_TREE, ACC_ALL = 1, 2, 3
+MESH_DELTA, MESH_PHI = 0, 1
+
+EXPORTED = ["dzs_params_default", "dzs_footprint_bytes", "dzs_create", "dzs_ics", "dzs_step",
+            "dzs_run_stages", "dzs_lightcone_drain", "dzs_destroy", "dzs_get_count", "dzs_get_state",
+            "dzs_set_state", "dzs_accel", "dzs_merge_only", "dzs_diagnostics", "dzs_get_tables",
+            "dzs_get_mesh", "dzs_get_counters", "dzs_set_profiling", "dzs_get_profile",
+            "dzs_last_error"]
+PROF_NAMES = ["kick_drift", "sort", "merge", "tree", "pm", "walk"]
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("n1d", C.c_int32), ("mesh", C.c_int32), ("box", C.c_double),
+        ("omega_m", C.c_double), ("omega_l", C.c_double), ("hubble", C.c_double),
+        ("sigma8", C.c_double), ("ns", C.c_double), ("z_init", C.c_double),
+        ("nsteps", C.c_int32), ("leaf_bucket", C.c_int32), ("walk_group", C.c_int32),
+        ("dzs_on", C.c_int32), ("merge_level", C.c_int32), ("rlc_mode", C.c_int32),
+        ("rs_cells", C.c_double), ("rcut_rs", C.c_double), ("theta", C.c_double),
+        ("soft_frac", C.c_double), ("theta_dzs", C.c_double), ("buffer_cells", C.c_double),
+        ("seed", C.c_uint64), ("precision", C.c_int32), ("device", C.c_int32),
+        ("lc_capacity", C.c_uint64),
+    ]
+
+
+RECORD_DTYPE = np.dtype([("id", "<u4"), ("k", "<u4"), ("a_cross", "<f8"),
+                         ("x", "<f8", (3,)), ("p", "<f8", (3,))])
+
+_lib = None
+
+
+class DzsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES[status] if 0 <= status < 8 else status, msg))
+        self.status = status
+
+
+def load(path: str = LIB_PATH):
+    """Load libdzs.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libdzs.so not built: run paper_2005_05328_gb300.build.build() "
+                           "(or __graft_entry__.build()) first")
+    L = C.CDLL(path)
+    vp, sz, i32, u32, u64 = C.c_void_p, C.c_size_t, C.c_int32, C.c_uint32, C.c_uint64
+    P = C.POINTER(Params)
+    sig = {
+        "dzs_params_default": [P], "dzs_footprint_bytes": [P, C.POINTER(sz)],
+        "dzs_create": [P, vp, C.POINTER(vp)], "dzs_ics": [vp],
+        "dzs_step": [vp, i32, C.POINTER(i32)], "dzs_run_stages": [vp, u32],
+        "dzs_lightcone_drain": [vp, vp, sz, C.POINTER(sz)], "dzs_destroy": [vp],
+        "dzs_get_count": [vp, C.POINTER(sz), C.POINTER(i32)],
+        "dzs_get_state": [vp, vp, vp, vp, vp, vp, vp, sz, C.POINTER(sz)],
+        "dzs_set_state": [vp, vp, vp, vp, vp, vp, vp, sz, i32],
+        "dzs_accel": [vp, i32, vp], "dzs_merge_only": [vp, u64], "dzs_diagnostics": [vp, vp],
+        "dzs_get_tables": [vp, vp, vp, vp, vp, vp, vp], "dzs_get_mesh": [vp, i32, vp],
+        "dzs_get_counters": [vp, vp], "dzs_set_profiling": [vp, i32], "dzs_get_profile": [vp, vp, vp],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = C.c_int
+    L.dzs_last_error.argtypes = [vp]
+    L.dzs_last_error.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _check(status, ctx):
+    if status != DZS_OK:
+        msg = load().dzs_last_error(ctx)
+        raise DzsError(status, msg.decode() if msg else "")
+
+
+def params(**kw) -> Params:
+    p = Params()
+    load().dzs_params_default(C.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def dzs_footprint_bytes(p: Params) -> int:
+    out = C.c_size_t(0)
+    _check(load().dzs_footprint_bytes(C.byref(p), C.byref(out)), None)
+    return out.value
+
+
+def dzs_create(p: Params, stream: int = 0):
+    h = C.c_void_p()
+    _check(load().dzs_create(C.byref(p), C.c_void_p(stream), C.byref(h)), None)
+    return h
+
+
+def dzs_destroy(h):
+    load().dzs_destroy(h)
+
+
+def dzs_ics(h):
+    _check(load().dzs_ics(h), h)
+
+
+def dzs_step(h, n: int) -> int:
+    done = C.c_int32(0)
+    _check(load().dzs_step(h, n, C.byref(done)), h)
+    return done.value
+
+
+def dzs_run_stages(h, mask: int):
+    _check(load().dzs_run_stages(h, mask), h)
+
+
+def dzs_get_count(h):
+    n = C.c_size_t(0)
+    st = C.c_int32(0)
+    _check(load().dzs_get_count(h, C.byref(n), C.byref(st)), h)
+    return n.value, st.value
+
+
+def dzs_lightcone_drain(h, cap: int = 1 << 22):
+    buf = np.zeros(cap, RECORD_DTYPE)
+    n = C.c_size_t(0)
+    _check(load().dzs_lightcone_drain(h, _ptr(buf), cap, C.byref(n)), h)
+    return buf[:n.value].copy()
+
+
+def dzs_get_state(h, cap: int = None):
+    n, _ = dzs_get_count(h)
+    u = np.zeros(3 * n, np.uint32)
+    p = np.zeros(3 * n)
+    g = np.zeros(3 * n)
+    k = np.zeros(n, np.uint32)
+    i = np.zeros(n, np.uint32)
+    fl = np.zeros(n, np.uint8)
+    nn = C.c_size_t(0)
+    _check(load().dzs_get_state(h, _ptr(u), _ptr(p), _ptr(g), _ptr(k), _ptr(i), _ptr(fl), n, C.byref(nn)), h)
+    return dict(u=u.reshape(3, n), p=p.reshape(3, n), g=g.reshape(3, n), k=k, id=i, fl=fl)
+
+
+def dzs_set_state(h, state: dict, step: int, with_g: bool = True):
+    u = np.ascontiguousarray(state["u"], np.uint32)
+    n = u.shape[1]
+    p = np.ascontiguousarray(state["p"], np.float64)
+    g = np.ascontiguousarray(state["g"], np.float64) if (with_g and "g" in state) else None
+    k = np.ascontiguousarray(state["k"], np.uint32)
+    i = np.ascontiguousarray(state["id"], np.uint32)
+    fl = np.ascontiguousarray(state["fl"], np.uint8)
+    _check(load().dzs_set_state(h, _ptr(u), _ptr(p), _ptr(g), _ptr(k), _ptr(i), _ptr(fl), n, step), h)
+
+
+def dzs_accel(h, parts: int = ACC_ALL):
+    n, _ = dzs_get_count(h)
+    g = np.zeros(3 * n)
+    _check(load().dzs_accel(h, parts, _ptr(g)), h)
+    return g.reshape(3, n)
+
+
+def dzs_merge_only(h, rlat: int):
+    _check(load().dzs_merge_only(h, int(rlat)), h)
+
+
+def dzs_diagnostics(h):
+    out = np.zeros(8)
+    _check(load().dzs_diagnostics(h, _ptr(out)), h)
+    return out
+
+
+def dzs_get_tables(h, nsteps: int):
+    a = np.zeros(nsteps + 1); dr = np.zeros(nsteps); k1 = np.zeros(nsteps); k2 = np.zeros(nsteps)
+    rlc = np.zeros(nsteps + 1); rlat = np.zeros(nsteps + 1, np.uint64)
+    _check(load().dzs_get_tables(h, _ptr(a), _ptr(dr), _ptr(k1), _ptr(k2), _ptr(rlc), _ptr(rlat)), h)
+    return dict(a=a, drift=dr, kick1=k1, kick2=k2, rlc=rlc, rlat=rlat)
+
+
+def dzs_get_mesh(h, which: int, mesh: int):
+    out = np.zeros(mesh ** 3)
+    _check(load().dzs_get_mesh(h, which, _ptr(out)), h)
+    return out.reshape(mesh, mesh, mesh)
+
+
+def dzs_set_profiling(h, enable: bool):
+    _check(load().dzs_set_profiling(h, 1 if enable else 0), h)
+
+
+def dzs_get_profile(h):
+    ms = np.zeros(len(PROF_NAMES))
+    calls = np.zeros(len(PROF_NAMES), np.uint64)
+    _check(load().dzs_get_profile(h, _ptr(ms), _ptr(calls)), h)
+    return {name: (float(ms[i]), int(calls[i])) for i, name in enumerate(PROF_NAMES)}
+
+
+def dzs_get_counters(h):
+    out = np.zeros(6, np.uint64)
+    _check(load().dzs_get_counters(h, _ptr(out)), h)
+    return out
+
+
+class Context:
+    """Owns one dzs_ctx; methods mirror the C entry points."""
+
+    def __init__(self, p: Params = None, stream: int = 0, **kw):
+        self.params = p if p is not None else params(**kw)
+        self.h = dzs_create(self.params, stream)
+
+    def close(self):
+        if self.h:
+            dzs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def ics(self): dzs_ics(self.h)
+    def step(self, n=1): return dzs_step(self.h, n)
+    def run_stages(self, mask): dzs_run_stages(self.h, mask)
+    def count(self): return dzs_get_count(self.h)
+    def drain(self, cap=1 << 22): return dzs_lightcone_drain(self.h, cap)
+    def state(self): return dzs_get_state(self.h)
+    def set_state(self, st, step, with_g=True): dzs_set_state(self.h, st, step, with_g)
+    def accel(self, parts=ACC_ALL): return dzs_accel(self.h, parts)
+    def merge_only(self, rlat): dzs_merge_only(self.h, rlat)
+    def diagnostics(self): return dzs_diagnostics(self.h)
+    def tables(self): return dzs_get_tables(self.h, self.params.nsteps)
+    def mesh(self, which): return dzs_get_mesh(self.h, which, self.params.mesh)
+    def counters(self): return dzs_get_counters(self.h)
+    def set_profiling(self, on=True): dzs_set_profiling(self.h, on)
+    def profile(self): return dzs_get_profile(self.h)

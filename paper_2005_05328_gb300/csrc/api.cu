@@ -1,0 +1,698 @@
+// api.cu -- the C ABI of include/dzs.h: context life cycle, state injection
+// and extraction, the stage runner of one KDK step, lightcone drain and
+// diagnostics.  Step order (paper Sec. 2.2: DZS on global steps, tree rebuilt
+// and forces recomputed after a merge): opening kick + drift + crossing ->
+// records -> Morton sort -> merge -> tree -> PM -> walk + closing kick.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "common.cuh"
+
+using namespace dzs;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+
+int ilog2i(int64_t v) {
+  int l = 0;
+  while ((1ll << l) < v) ++l;
+  return l;
+}
+
+const char* validate(const dzs_params* p) {
+  if (!p) return "params is NULL";
+  if (!is_pow2(p->n1d) || p->n1d < 2 || p->n1d > 512) return "n1d must be a power of two in [2, 512]";
+  if (!is_pow2(p->mesh) || p->mesh < 8 || p->mesh > 512) return "mesh must be a power of two in [8, 512]";
+  if (!(p->box > 0)) return "box must be positive";
+  if (!(p->omega_m > 0) || !(p->omega_l >= 0)) return "omega_m > 0 and omega_l >= 0 required";
+  if (!(p->hubble > 0) || !(p->sigma8 >= 0)) return "hubble > 0 and sigma8 >= 0 required";
+  if (!(p->z_init > 0)) return "z_init must be positive";
+  if (p->nsteps < 1 || p->nsteps > 100000) return "nsteps out of range";
+  if (p->leaf_bucket < 1 || p->leaf_bucket > 14) return "leaf_bucket must be in [1, 14]";
+  if (p->walk_group < p->leaf_bucket || p->walk_group > 64) return "walk_group must be in [leaf_bucket, 64]";
+  if (p->merge_level < 1 || (1 << (p->merge_level - 1)) > p->n1d) return "merge_level out of range";
+  if (!(p->rs_cells > 0) || !(p->rcut_rs > 0)) return "rs_cells and rcut_rs must be positive";
+  if (!(p->theta > 0)) return "theta must be positive";
+  if (!(p->soft_frac > 0)) return "soft_frac must be positive";
+  if (!(p->theta_dzs > 0)) return "theta_dzs must be positive";
+  if (!(p->buffer_cells >= 0)) return "buffer_cells must be >= 0";
+  if (p->rlc_mode != DZS_RLC_SWEEP && p->rlc_mode != DZS_RLC_PHYSICAL) return "unknown rlc_mode";
+  if (p->precision != DZS_FP32 && p->precision != DZS_FP64) return "unknown precision";
+  return nullptr;
+}
+
+struct Layout {
+  size_t total = 0;
+  size_t take(size_t bytes) {
+    size_t off = total;
+    total += (bytes + 255) & ~size_t(255);
+    return off;
+  }
+};
+
+// offsets of every device buffer in the arena (also used for the footprint)
+struct Plan {
+  int64_t cap, node_cap, m3, nspec, nb, nchunks, ring;
+  size_t rsz;
+  size_t o_u, o_u2, o_p, o_p2, o_g, o_gsave, o_k, o_k2, o_id, o_id2, o_fl, o_fl2, o_key, o_key2, o_idx, o_idx2, o_hist,
+      o_blocksum, o_iscan, o_prefix, o_mend, o_nodes, o_lvl, o_nsum, o_groups, o_ghead, o_rho, o_spec, o_phi,
+      o_cstart, o_tw, o_green, o_ring, o_n, o_err, o_counters, o_diag, o_convert;
+  size_t total;
+  explicit Plan(const dzs_params& P) {
+    cap = (int64_t)P.n1d * P.n1d * P.n1d;
+    node_cap = 2 * cap + 1024;
+    m3 = (int64_t)P.mesh * P.mesh * P.mesh;
+    nspec = (int64_t)P.mesh * P.mesh * (P.mesh / 2 + 1);
+    nb = (cap + 2047) / 2048;
+    nchunks = (cap + 1024) / 1024 + 1;
+    ring = P.lc_capacity ? (int64_t)P.lc_capacity : cap;
+    rsz = P.precision == DZS_FP64 ? 8 : 4;
+    Layout L;
+    o_u = L.take(12 * cap);
+    o_u2 = L.take(12 * cap);
+    o_p = L.take(3 * rsz * cap);
+    o_p2 = L.take(3 * rsz * cap);
+    o_g = L.take(3 * rsz * cap);
+    o_gsave = L.take(3 * rsz * cap);
+    o_k = L.take(4 * cap);
+    o_k2 = L.take(4 * cap);
+    o_id = L.take(4 * cap);
+    o_id2 = L.take(4 * cap);
+    o_fl = L.take(cap);
+    o_fl2 = L.take(cap);
+    o_key = L.take(8 * cap);
+    o_key2 = L.take(8 * cap);
+    o_idx = L.take(4 * cap);
+    o_idx2 = L.take(4 * cap);
+    o_hist = L.take(4 * (257 * nb + 256));
+    o_blocksum = L.take(8 * 4 * (nchunks + 2));
+    o_iscan = L.take(4 * (2 * cap + 4));
+    o_prefix = L.take(8 * 4 * (cap + 1));
+    o_mend = L.take(4 * cap);
+    o_nodes = L.take(sizeof(Node) * node_cap);
+    o_lvl = L.take(4 * 32);
+    o_nsum = L.take(8 * 3 * node_cap);
+    o_groups = L.take(4 * cap);
+    o_ghead = L.take(4 * cap);
+    o_rho = L.take(rsz * m3);
+    o_spec = L.take(2 * rsz * nspec);
+    o_phi = L.take(rsz * m3);
+    o_cstart = L.take(4 * (m3 + 1));
+    o_tw = L.take(2 * rsz * (P.mesh / 2 + 1));
+    o_green = L.take(rsz * (2 * P.mesh + 1));
+    o_ring = L.take(sizeof(dzs_lc_record) * ring);
+    o_n = L.take(16);
+    o_err = L.take(16);
+    o_counters = L.take(8 * 16);
+    o_diag = L.take(8 * (8 + 3 * 304));
+    o_convert = L.take(8 * 3 * cap);
+    total = L.total;
+  }
+};
+
+#define CK(call)                                                                   \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess) return fail(c, DZS_ECUDA, #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+dzs_status fail(dzs_ctx* c, dzs_status s, const char* what, const char* detail = nullptr) {
+  std::string m = what ? what : "";
+  if (detail) m += std::string(": ") + detail;
+  if (c) {
+    c->err = m;
+    if (s == DZS_EDEVICE || s == DZS_ETIMEOUT) c->poisoned = true;
+  } else {
+    g_create_error = m;
+  }
+  return s;
+}
+
+dzs_status check_device_errors(dzs_ctx* c) {
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return fail(c, DZS_EDEVICE, "device failure", cudaGetErrorString(e));
+  uint32_t err = 0;
+  e = cudaMemcpy(&err, c->B.err, sizeof(uint32_t), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return fail(c, DZS_EDEVICE, "device failure", cudaGetErrorString(e));
+  if (err & (kErrNodes | kErrStack | kErrGroups)) {
+    char buf[160];
+    snprintf(buf, sizeof buf, "device buffer overflow (error word 0x%x)", err);
+    return fail(c, DZS_EOVERFLOW, buf);
+  }
+  return DZS_OK;
+}
+
+dzs_status guard(dzs_ctx* c) {
+  if (!c) return DZS_EINVAL;
+  if (c->poisoned) return fail(c, DZS_ESTATE, "context poisoned by an earlier device failure");
+  cudaError_t e = cudaSetDevice(c->dev);
+  if (e != cudaSuccess) return fail(c, DZS_ECUDA, "cudaSetDevice", cudaGetErrorString(e));
+  return DZS_OK;
+}
+
+// per-stage event pair on the context stream (no synchronisation)
+cudaEvent_t prof_event(dzs_ctx* c) {
+  if (!c->ev_pool.empty()) {
+    cudaEvent_t e = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+struct ProfScope {
+  dzs_ctx* c;
+  int cat;
+  cudaEvent_t a = nullptr;
+  ProfScope(dzs_ctx* cc, int k) : c(cc), cat(k) {
+    if (c->prof_on) {
+      a = prof_event(c);
+      cudaEventRecord(a, c->stream);
+    }
+  }
+  ~ProfScope() {
+    if (c->prof_on && a) {
+      cudaEvent_t b = prof_event(c);
+      cudaEventRecord(b, c->stream);
+      c->prof_pending.push_back({cat, a, b});
+    }
+  }
+};
+
+// forces of the current (sorted) particle set: tree, PM, walk (+ closing kick)
+void run_force(dzs_ctx* c, int parts, bool close_kick) {
+  {
+    ProfScope ps(c, DZS_PROF_TREE);
+    launch_tree(c);  // also lists the groups the walk needs
+  }
+  {
+    ProfScope ps(c, DZS_PROF_PM);
+    if (parts & DZS_ACC_PM)
+      launch_pm(c, true);
+    else
+      cudaMemsetAsync(c->B.g, 0, 3 * c->cap * (c->fp64 ? 8 : 4), c->stream);
+  }
+  ProfScope ps(c, DZS_PROF_WALK);
+  launch_walk(c, (parts & DZS_ACC_TREE) != 0, close_kick, c->step);
+}
+
+// forces of the current state in its current order (sorts a copy of the
+// order, computes, restores the order); g in double, stride n, in convert
+void force_in_order(dzs_ctx* c, int parts) {
+  launch_keys(c);
+  launch_sort(c);
+  run_force(c, parts, false);
+  launch_unpermute(c, (double*)c->B.convert);
+}
+
+}  // namespace
+
+extern "C" {
+
+dzs_status dzs_params_default(dzs_params* p) {
+  if (!p) return DZS_EINVAL;
+  memset(p, 0, sizeof(*p));
+  p->n1d = 32;
+  p->mesh = 64;
+  p->box = 64.0;
+  p->omega_m = 0.3;
+  p->omega_l = 0.7;
+  p->hubble = 0.7;
+  p->sigma8 = 0.8;
+  p->ns = 0.96;
+  p->z_init = 49.0;
+  p->nsteps = 96;
+  p->leaf_bucket = 8;
+  p->walk_group = 32;
+  p->dzs_on = 1;
+  p->merge_level = 2;
+  p->rlc_mode = DZS_RLC_SWEEP;
+  p->rs_cells = 1.25;
+  p->rcut_rs = 4.5;
+  p->theta = 0.5;
+  p->soft_frac = 1.0 / 40.0;
+  p->theta_dzs = 0.1;
+  p->buffer_cells = 2.0;
+  p->seed = 1;
+  p->precision = DZS_FP32;
+  p->device = 0;
+  p->lc_capacity = 0;
+  return DZS_OK;
+}
+
+dzs_status dzs_footprint_bytes(const dzs_params* p, size_t* bytes) {
+  const char* why = validate(p);
+  if (why || !bytes) return fail(nullptr, DZS_EINVAL, why ? why : "bytes is NULL");
+  *bytes = Plan(*p).total;
+  return DZS_OK;
+}
+
+dzs_status dzs_create(const dzs_params* p, void* cuda_stream, dzs_ctx** out) {
+  if (!out) return fail(nullptr, DZS_EINVAL, "out is NULL");
+  *out = nullptr;
+  const char* why = validate(p);
+  if (why) return fail(nullptr, DZS_EINVAL, why);
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || p->device < 0 || p->device >= ndev)
+    return fail(nullptr, DZS_EDEVICE, "no such CUDA device");
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, p->device) != cudaSuccess) return fail(nullptr, DZS_EDEVICE, "device query");
+  if (!(prop.major == 10 && prop.minor == 3))
+    return fail(nullptr, DZS_EDEVICE, "this library is built for sm_103a (GB300) only");
+  dzs_ctx* c = new (std::nothrow) dzs_ctx();
+  if (!c) return fail(nullptr, DZS_ENOMEM, "host allocation");
+  c->P = *p;
+  c->dev = p->device;
+  c->stream = (cudaStream_t)cuda_stream;
+  c->fp64 = p->precision == DZS_FP64;
+  c->n1 = p->n1d;
+  c->N0 = (int64_t)p->n1d * p->n1d * p->n1d;
+  c->cap = c->N0;
+  c->M = p->mesh;
+  c->logM = ilog2i(p->mesh);
+  c->lat = 4294967296.0 / p->box;
+  c->scale = p->box / 4294967296.0;
+  c->gm0 = 1.5 * p->omega_m * p->box * p->box * p->box / (4.0 * M_PI * (double)c->N0);
+  c->eps0 = p->soft_frac * p->box / p->n1d;
+  c->rs = p->rs_cells * p->box / p->mesh;
+  c->rcut = p->rcut_rs * c->rs;
+  {
+    // same operation order as the definition r_cut / L * 2^32
+    double rcut_lat = p->rcut_rs * c->rs / p->box * 4294967296.0;
+    c->rcut_lat2 = rcut_lat * rcut_lat;
+  }
+  int j = 1;
+  while (((int64_t)1 << j) * ((int64_t)1 << (p->merge_level - 1)) < p->n1d) ++j;
+  c->jmin = j;
+  c->blat = (uint64_t)std::floor(p->buffer_cells * 4294967296.0 / p->mesh);
+  for (int l = 0; l <= kMaxLevel; ++l) {
+    double lovt = std::ceil(std::ldexp(1.0, 32 - l) / p->theta_dzs);
+    c->merge_thr[l] = (lovt < 4294967296.0) ? c->blat + (uint64_t)lovt : ~0ull;
+  }
+  compute_tables(c->P, c->T);
+  Plan pl(*p);
+  c->node_cap = pl.node_cap;
+  c->ring_cap = (size_t)pl.ring;
+  dzs_status st = DZS_OK;
+  if (cudaSetDevice(c->dev) != cudaSuccess) {
+    delete c;
+    return fail(nullptr, DZS_EDEVICE, "cudaSetDevice");
+  }
+  cudaError_t e = cudaMalloc((void**)&c->arena, pl.total);
+  if (e != cudaSuccess) {
+    delete c;
+    return fail(nullptr, DZS_ENOMEM, "device arena", cudaGetErrorString(e));
+  }
+  c->arena_bytes = pl.total;
+  char* a = c->arena;
+  Buffers& B = c->B;
+  B.u = (uint32_t*)(a + pl.o_u);
+  B.u2 = (uint32_t*)(a + pl.o_u2);
+  B.p = a + pl.o_p;
+  B.p2 = a + pl.o_p2;
+  B.g = a + pl.o_g;
+  B.gsave = a + pl.o_gsave;
+  B.k = (uint32_t*)(a + pl.o_k);
+  B.k2 = (uint32_t*)(a + pl.o_k2);
+  B.id = (uint32_t*)(a + pl.o_id);
+  B.id2 = (uint32_t*)(a + pl.o_id2);
+  B.fl = (uint8_t*)(a + pl.o_fl);
+  B.fl2 = (uint8_t*)(a + pl.o_fl2);
+  B.key = (uint64_t*)(a + pl.o_key);
+  B.key2 = (uint64_t*)(a + pl.o_key2);
+  B.idx = (uint32_t*)(a + pl.o_idx);
+  B.idx2 = (uint32_t*)(a + pl.o_idx2);
+  B.hist = (uint32_t*)(a + pl.o_hist);
+  B.blocksum = (int64_t*)(a + pl.o_blocksum);
+  B.iscan = (int32_t*)(a + pl.o_iscan);
+  B.prefix = (uint64_t*)(a + pl.o_prefix);
+  B.mend = (int32_t*)(a + pl.o_mend);
+  B.nodes = (Node*)(a + pl.o_nodes);
+  B.lvl_count = (int32_t*)(a + pl.o_lvl);
+  B.nsum = (uint64_t*)(a + pl.o_nsum);
+  B.groups = (int32_t*)(a + pl.o_groups);
+  B.group_head = (int32_t*)(a + pl.o_ghead);
+  B.rho = a + pl.o_rho;
+  B.spec = a + pl.o_spec;
+  B.phi = a + pl.o_phi;
+  B.cell_start = (int32_t*)(a + pl.o_cstart);
+  B.twiddle = a + pl.o_tw;
+  B.green_axis = a + pl.o_green;
+  B.ring = (dzs_lc_record*)(a + pl.o_ring);
+  B.n = (int32_t*)(a + pl.o_n);
+  B.err = (uint32_t*)(a + pl.o_err);
+  B.counters = (uint64_t*)(a + pl.o_counters);
+  B.diag = (double*)(a + pl.o_diag);
+  B.convert = a + pl.o_convert;
+  if (cudaMemset(B.n, 0, 16) != cudaSuccess || cudaMemset(B.err, 0, 16) != cudaSuccess ||
+      cudaMemset(B.counters, 0, 8 * 16) != cudaSuccess) {
+    cudaFree(c->arena);
+    delete c;
+    return fail(nullptr, DZS_ECUDA, "arena init");
+  }
+  launch_fft_init(c);
+  if (cudaDeviceSynchronize() != cudaSuccess) st = DZS_ECUDA;
+  if (st != DZS_OK) {
+    cudaFree(c->arena);
+    delete c;
+    return fail(nullptr, st, "context init");
+  }
+  *out = c;
+  return DZS_OK;
+}
+
+dzs_status dzs_destroy(dzs_ctx* c) {
+  if (!c) return DZS_OK;
+  cudaSetDevice(c->dev);
+  cudaStreamSynchronize(c->stream);
+  for (auto& pe : c->prof_pending) {
+    cudaEventDestroy(pe.a);
+    cudaEventDestroy(pe.b);
+  }
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  if (c->arena) cudaFree(c->arena);
+  delete c;
+  return DZS_OK;
+}
+
+dzs_status dzs_ics(dzs_ctx* c) {
+  dzs_status s = guard(c);
+  if (s) return s;
+  CK(cudaMemsetAsync(c->B.counters, 0, 8 * 16, c->stream));
+  CK(cudaMemsetAsync(c->B.err, 0, 16, c->stream));
+  c->drained = 0;
+  launch_ics(c);
+  c->step = 0;
+  launch_keys(c);
+  launch_sort(c);
+  run_force(c, DZS_ACC_ALL, false);
+  c->have_state = true;
+  CK(cudaGetLastError());
+  return check_device_errors(c);
+}
+
+dzs_status dzs_run_stages(dzs_ctx* c, uint32_t mask) {
+  dzs_status s = guard(c);
+  if (s) return s;
+  if (!c->have_state) return fail(c, DZS_ESTATE, "no particle state (call dzs_ics or dzs_set_state)");
+  if (c->step >= c->P.nsteps && (mask & (DZS_STAGE_KICK_DRIFT | DZS_STAGE_CLOSE | DZS_STAGE_MERGE)))
+    return fail(c, DZS_ESTATE, "the run has reached a = 1");
+  const int st = c->step;
+  if (mask & DZS_STAGE_KICK_DRIFT) {
+    ProfScope ps(c, DZS_PROF_KICK_DRIFT);
+    launch_kick_drift(c, st, true, true);
+    launch_records(c, st);
+  }
+  if (mask & DZS_STAGE_SORT) {
+    ProfScope ps(c, DZS_PROF_SORT);
+    if (!(mask & DZS_STAGE_KICK_DRIFT)) launch_keys(c);
+    launch_sort(c);
+  }
+  if ((mask & DZS_STAGE_MERGE) && c->P.dzs_on) {
+    ProfScope ps(c, DZS_PROF_MERGE);
+    launch_merge(c, c->T.rlat[st + 1]);
+  }
+  if (mask & DZS_STAGE_FORCE) {
+    run_force(c, DZS_ACC_ALL, (mask & DZS_STAGE_CLOSE) != 0);
+  } else if (mask & DZS_STAGE_CLOSE) {
+    ProfScope ps(c, DZS_PROF_WALK);
+    launch_close_kick(c, st);
+  }
+  if (mask & DZS_STAGE_CLOSE) c->step = st + 1;
+  CK(cudaGetLastError());
+  return DZS_OK;
+}
+
+dzs_status dzs_step(dzs_ctx* c, int32_t nsteps, int32_t* steps_done) {
+  dzs_status s = guard(c);
+  if (s) return s;
+  if (steps_done) *steps_done = 0;
+  if (nsteps < 0) return fail(c, DZS_EINVAL, "nsteps < 0");
+  int done = 0;
+  while (done < nsteps && c->step < c->P.nsteps) {
+    s = dzs_run_stages(c, DZS_STAGE_ALL);
+    if (s) return s;
+    ++done;
+  }
+  if (steps_done) *steps_done = done;
+  return DZS_OK;
+}
+
+dzs_status dzs_lightcone_drain(dzs_ctx* c, dzs_lc_record* host_buf, size_t cap, size_t* n_out) {
+  dzs_status s = guard(c);
+  if (s) return s;
+  if (n_out) *n_out = 0;
+  if (!host_buf && cap) return fail(c, DZS_EINVAL, "host_buf is NULL");
+  s = check_device_errors(c);
+  if (s) return s;
+  uint64_t ctr[2];
+  CK(cudaMemcpy(ctr, c->B.counters, sizeof ctr, cudaMemcpyDeviceToHost));
+  uint64_t avail = ctr[0] - c->drained;
+  uint64_t take = avail < cap ? avail : cap;
+  uint64_t done = 0;
+  while (done < take) {
+    uint64_t slot = (c->drained + done) % c->ring_cap;
+    uint64_t chunk = c->ring_cap - slot;
+    if (chunk > take - done) chunk = take - done;
+    CK(cudaMemcpy(host_buf + done, c->B.ring + slot, chunk * sizeof(dzs_lc_record), cudaMemcpyDeviceToHost));
+    done += chunk;
+  }
+  c->drained += take;
+  if (n_out) *n_out = (size_t)take;
+  if (ctr[1]) {
+    char buf[128];
+    snprintf(buf, sizeof buf, "%llu lightcone records dropped (ring full)", (unsigned long long)ctr[1]);
+    return fail(c, DZS_EOVERFLOW, buf);
+  }
+  return DZS_OK;
+}
+
+dzs_status dzs_get_count(dzs_ctx* c, size_t* n, int32_t* step) {
+  dzs_status s = guard(c);
+  if (s) return s;
+  s = check_device_errors(c);
+  if (s) return s;
+  int32_t hn = 0;
+  CK(cudaMemcpy(&hn, c->B.n, sizeof hn, cudaMemcpyDeviceToHost));
+  if (n) *n = (size_t)hn;
+  if (step) *step = c->step;
+  return DZS_OK;
+}
+
+dzs_status dzs_get_state(dzs_ctx* c, uint32_t* u, double* p, double* g, uint32_t* k, uint32_t* id, uint8_t* fl,
+                         size_t cap, size_t* n_out) {
+  size_t n = 0;
+  dzs_status s = dzs_get_count(c, &n, nullptr);
+  if (s) return s;
+  if (n_out) *n_out = n;
+  if (n > cap) return fail(c, DZS_EINVAL, "cap smaller than the particle count");
+  double* conv = (double*)c->B.convert;
+  for (int ax = 0; ax < 3; ++ax) {
+    if (u) CK(cudaMemcpy(u + ax * n, c->B.u + ax * c->cap, 4 * n, cudaMemcpyDeviceToHost));
+  }
+  if (p) {
+    launch_to_double(c, c->B.p, 3 * c->cap, conv);
+    CK(cudaStreamSynchronize(c->stream));
+    for (int ax = 0; ax < 3; ++ax)
+      CK(cudaMemcpy(p + ax * n, conv + ax * c->cap, 8 * n, cudaMemcpyDeviceToHost));
+  }
+  if (g) {
+    launch_to_double(c, c->B.g, 3 * c->cap, conv);
+    CK(cudaStreamSynchronize(c->stream));
+    for (int ax = 0; ax < 3; ++ax)
+      CK(cudaMemcpy(g + ax * n, conv + ax * c->cap, 8 * n, cudaMemcpyDeviceToHost));
+  }
+  if (k) CK(cudaMemcpy(k, c->B.k, 4 * n, cudaMemcpyDeviceToHost));
+  if (id) CK(cudaMemcpy(id, c->B.id, 4 * n, cudaMemcpyDeviceToHost));
+  if (fl) {
+    CK(cudaMemcpy(fl, c->B.fl, n, cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < n; ++i) fl[i] &= (uint8_t)(DZS_FL_CROSSED | DZS_FL_MERGED);
+  }
+  return DZS_OK;
+}
+
+dzs_status dzs_set_state(dzs_ctx* c, const uint32_t* u, const double* p, const double* g, const uint32_t* k,
+                         const uint32_t* id, const uint8_t* fl, size_t n, int32_t step) {
+  dzs_status s = guard(c);
+  if (s) return s;
+  if (n > (size_t)c->cap) return fail(c, DZS_EINVAL, "n exceeds n1d^3");
+  if (n > 0 && (!u || !p || !k || !id || !fl)) return fail(c, DZS_EINVAL, "NULL state array");
+  if (step < 0 || step > c->P.nsteps) return fail(c, DZS_EINVAL, "step out of range");
+  CK(cudaStreamSynchronize(c->stream));
+  double* conv = (double*)c->B.convert;
+  for (int ax = 0; ax < 3; ++ax) {
+    CK(cudaMemcpy(c->B.u + ax * c->cap, u + ax * n, 4 * n, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(conv + ax * c->cap, p + ax * n, 8 * n, cudaMemcpyHostToDevice));
+  }
+  launch_from_double(c, conv, 3 * c->cap, c->B.p);
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaMemcpy(c->B.k, k, 4 * n, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(c->B.id, id, 4 * n, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(c->B.fl, fl, n, cudaMemcpyHostToDevice));
+  int32_t nn = (int32_t)n;
+  CK(cudaMemcpy(c->B.n, &nn, sizeof nn, cudaMemcpyHostToDevice));
+  CK(cudaMemset(c->B.err, 0, 16));
+  CK(cudaMemset(c->B.counters + 4, 0, sizeof(uint64_t)));
+  c->step = step;
+  c->have_state = true;
+  if (g) {
+    for (int ax = 0; ax < 3; ++ax)
+      CK(cudaMemcpy(conv + ax * c->cap, g + ax * n, 8 * n, cudaMemcpyHostToDevice));
+    launch_from_double(c, conv, 3 * c->cap, c->B.g);
+  } else {
+    force_in_order(c, DZS_ACC_ALL);  // g (double, stride n) in convert
+    size_t rs = c->fp64 ? 8 : 4;
+    for (int ax = 0; ax < 3; ++ax)
+      launch_from_double(c, conv + ax * n, (int64_t)n, (char*)c->B.g + ax * c->cap * rs);
+  }
+  CK(cudaGetLastError());
+  return check_device_errors(c);
+}
+
+dzs_status dzs_accel(dzs_ctx* c, int32_t parts, double* g_out) {
+  dzs_status s = guard(c);
+  if (s) return s;
+  if (!g_out || parts < 1 || parts > 3) return fail(c, DZS_EINVAL, "bad arguments");
+  if (!c->have_state) return fail(c, DZS_ESTATE, "no particle state");
+  size_t n = 0;
+  s = dzs_get_count(c, &n, nullptr);
+  if (s) return s;
+  // keep the state's g: force_in_order overwrites it
+  double* conv = (double*)c->B.convert;
+  size_t gbytes = 3 * c->cap * (c->fp64 ? 8 : 4);
+  CK(cudaMemcpyAsync(c->B.gsave, c->B.g, gbytes, cudaMemcpyDeviceToDevice, c->stream));
+  force_in_order(c, parts);
+  CK(cudaMemcpyAsync(c->B.g, c->B.gsave, gbytes, cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaGetLastError());
+  s = check_device_errors(c);
+  if (s) return s;
+  CK(cudaMemcpy(g_out, conv, 8 * 3 * n, cudaMemcpyDeviceToHost));
+  return DZS_OK;
+}
+
+dzs_status dzs_merge_only(dzs_ctx* c, uint64_t rlat) {
+  dzs_status s = guard(c);
+  if (s) return s;
+  if (!c->have_state) return fail(c, DZS_ESTATE, "no particle state");
+  launch_keys(c);
+  launch_merge(c, rlat);
+  CK(cudaGetLastError());
+  return check_device_errors(c);
+}
+
+dzs_status dzs_diagnostics(dzs_ctx* c, double out[8]) {
+  dzs_status s = guard(c);
+  if (s) return s;
+  if (!out) return fail(c, DZS_EINVAL, "out is NULL");
+  launch_diagnostics(c);
+  CK(cudaGetLastError());
+  s = check_device_errors(c);
+  if (s) return s;
+  CK(cudaMemcpy(out, c->B.diag, 8 * sizeof(double), cudaMemcpyDeviceToHost));
+  return DZS_OK;
+}
+
+dzs_status dzs_get_tables(dzs_ctx* c, double* a, double* drift, double* kick1, double* kick2, double* rlc,
+                          uint64_t* rlat) {
+  if (!c) return DZS_EINVAL;
+  size_t ns = (size_t)c->P.nsteps;
+  if (a) memcpy(a, c->T.a.data(), 8 * (ns + 1));
+  if (drift) memcpy(drift, c->T.drift.data(), 8 * ns);
+  if (kick1) memcpy(kick1, c->T.kick1.data(), 8 * ns);
+  if (kick2) memcpy(kick2, c->T.kick2.data(), 8 * ns);
+  if (rlc) memcpy(rlc, c->T.rlc.data(), 8 * (ns + 1));
+  if (rlat) memcpy(rlat, c->T.rlat.data(), 8 * (ns + 1));
+  return DZS_OK;
+}
+
+dzs_status dzs_get_mesh(dzs_ctx* c, int32_t which, double* out) {
+  dzs_status s = guard(c);
+  if (s) return s;
+  if (!out || (which != DZS_MESH_DELTA && which != DZS_MESH_PHI)) return fail(c, DZS_EINVAL, "bad arguments");
+  s = check_device_errors(c);
+  if (s) return s;
+  int64_t m3 = (int64_t)c->M * c->M * c->M;
+  const void* src = which == DZS_MESH_DELTA ? c->B.rho : c->B.phi;
+  if (c->fp64) {
+    CK(cudaMemcpy(out, src, 8 * m3, cudaMemcpyDeviceToHost));
+  } else {
+    float* tmp = new (std::nothrow) float[m3];
+    if (!tmp) return fail(c, DZS_ENOMEM, "host buffer");
+    cudaError_t e = cudaMemcpy(tmp, src, 4 * m3, cudaMemcpyDeviceToHost);
+    for (int64_t i = 0; i < m3 && e == cudaSuccess; ++i) out[i] = tmp[i];
+    delete[] tmp;
+    if (e != cudaSuccess) return fail(c, DZS_ECUDA, "mesh copy", cudaGetErrorString(e));
+  }
+  return DZS_OK;
+}
+
+dzs_status dzs_set_profiling(dzs_ctx* c, int32_t enable) {
+  dzs_status s = guard(c);
+  if (s) return s;
+  CK(cudaStreamSynchronize(c->stream));
+  for (auto& pe : c->prof_pending) {
+    c->ev_pool.push_back(pe.a);
+    c->ev_pool.push_back(pe.b);
+  }
+  c->prof_pending.clear();
+  for (int i = 0; i < 8; ++i) {
+    c->prof_ms[i] = 0;
+    c->prof_calls[i] = 0;
+  }
+  CK(cudaMemsetAsync(c->B.counters + 4, 0, sizeof(uint64_t), c->stream));
+  c->prof_on = enable != 0;
+  return DZS_OK;
+}
+
+dzs_status dzs_get_profile(dzs_ctx* c, double ms[DZS_PROF_N], uint64_t calls[DZS_PROF_N]) {
+  dzs_status s = guard(c);
+  if (s) return s;
+  CK(cudaStreamSynchronize(c->stream));
+  for (auto& pe : c->prof_pending) {
+    float t = 0;
+    CK(cudaEventElapsedTime(&t, pe.a, pe.b));
+    c->prof_ms[pe.cat] += t;
+    c->prof_calls[pe.cat] += 1;
+    c->ev_pool.push_back(pe.a);
+    c->ev_pool.push_back(pe.b);
+  }
+  c->prof_pending.clear();
+  for (int i = 0; i < DZS_PROF_N; ++i) {
+    if (ms) ms[i] = c->prof_ms[i];
+    if (calls) calls[i] = c->prof_calls[i];
+  }
+  return DZS_OK;
+}
+
+dzs_status dzs_get_counters(dzs_ctx* c, uint64_t out[6]) {
+  dzs_status s = guard(c);
+  if (s) return s;
+  if (!out) return fail(c, DZS_EINVAL, "out is NULL");
+  CK(cudaStreamSynchronize(c->stream));
+  uint64_t ctr[16];
+  uint32_t err = 0;
+  CK(cudaMemcpy(ctr, c->B.counters, sizeof ctr, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(&err, c->B.err, sizeof err, cudaMemcpyDeviceToHost));
+  out[0] = ctr[2];
+  out[1] = ctr[3];
+  out[2] = ctr[4];
+  out[3] = err;
+  out[4] = c->launches;
+  out[5] = ctr[0];
+  return DZS_OK;
+}
+
+const char* dzs_last_error(const dzs_ctx* c) {
+  if (!c) return g_create_error.c_str();
+  return c->err.c_str();
+}
+
+}  // extern "C"

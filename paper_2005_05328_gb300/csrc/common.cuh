@@ -1,0 +1,200 @@
+// common.cuh -- shared device helpers and the context layout of the DZS
+// TreePM library (paper: Garaldi, Nori & Baldi, arXiv 2005.05328).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "dzs.h"
+
+namespace dzs {
+
+constexpr int kThreads = 256;
+constexpr int kMaxLevel = 21;  // 21 Morton bits per axis
+
+// device error word bits (never a trap: kernels record and skip)
+enum : uint32_t {
+  kErrNodes = 1u,    // tree node capacity exceeded
+  kErrStack = 2u,    // walk stack overflow
+  kErrRing = 4u,     // lightcone ring full (records dropped)
+  kErrGroups = 8u,   // group capacity exceeded
+  kErrSort = 16u,    // inconsistent radix sort histogram
+  kErrCell = 32u,    // CIC cell start table inconsistent
+};
+
+// flag bits: bit 0 crossed (public), bit 1 merged (public), bit 2 crossed in
+// the current step (transient: cleared by the next opening kick)
+constexpr uint8_t kFlCrossed = 1, kFlMerged = 2, kFlNow = 4;
+
+__host__ __device__ inline uint64_t spread3(uint32_t v) {
+  uint64_t x = v & 0x1fffffu;
+  x = (x | (x << 32)) & 0x1f00000000ffffull;
+  x = (x | (x << 16)) & 0x1f0000ff0000ffull;
+  x = (x | (x << 8)) & 0x100f00f00f00f00full;
+  x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+  x = (x | (x << 2)) & 0x1249249249249249ull;
+  return x;
+}
+
+// 63-bit Morton key of the top 21 bits per axis; x takes the highest bit of
+// each 3-bit digit, so key >> 3(21 - j) is the octree cell at depth j
+__host__ __device__ inline uint64_t morton_key(uint32_t x, uint32_t y, uint32_t z) {
+  return (spread3(x >> 11) << 2) | (spread3(y >> 11) << 1) | spread3(z >> 11);
+}
+
+// squared lattice distance to the observer at 2^31 (exact, < 3 * 2^62)
+__host__ __device__ inline uint64_t dist2_obs(uint32_t x, uint32_t y, uint32_t z) {
+  int64_t a = (int32_t)(x - 0x80000000u), b = (int32_t)(y - 0x80000000u), c = (int32_t)(z - 0x80000000u);
+  return (uint64_t)(a * a) + (uint64_t)(b * b) + (uint64_t)(c * c);
+}
+
+template <class R>
+struct cplx {
+  R x, y;
+};
+
+template <class R>
+__device__ __forceinline__ cplx<R> cmul(cplx<R> a, cplx<R> b) {
+  return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+
+inline int grid_for(int64_t n, int threads = kThreads, int cap = 152 * 16) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  return (int)(b < cap ? b : cap);
+}
+
+// ---------------------------------------------------------------- context
+
+struct Tables {
+  std::vector<double> a, drift, kick1, kick2, rlc;
+  std::vector<uint64_t> rlat;
+  double dplus_i = 0, f_i = 0, e_i = 0, power_amp = 0;
+};
+
+// node record of the oct-tree, 48 bytes
+struct Node {
+  uint32_t cx, cy, cz;        // cube centre (lattice)
+  uint32_t comx, comy, comz;  // rounded integer centre of mass
+  uint32_t mass;              // sum of k
+  uint32_t kmax;              // largest member k (softening)
+  int32_t start, count;       // particle range
+  int32_t child;              // first child, -1 for a leaf
+  uint32_t meta;              // level (bits 0-7) | nchild (bits 8-15)
+};
+static_assert(sizeof(Node) == 48, "node layout");
+
+struct Buffers {
+  // particle state (primary and alternate for permutations / compaction)
+  uint32_t *u = nullptr, *u2 = nullptr;  // [3][cap]
+  void *p = nullptr, *p2 = nullptr;      // real [3][cap]
+  void* g = nullptr;                     // real [3][cap]
+  void* gsave = nullptr;                 // real [3][cap] (accelerations kept across dzs_accel)
+  uint32_t *k = nullptr, *k2 = nullptr, *id = nullptr, *id2 = nullptr;
+  uint8_t *fl = nullptr, *fl2 = nullptr;
+  // sort
+  uint64_t *key = nullptr, *key2 = nullptr;
+  uint32_t *idx = nullptr, *idx2 = nullptr;
+  uint32_t* hist = nullptr;  // [256][max blocks]
+  // generic scan scratch
+  int64_t* blocksum = nullptr;
+  int32_t* iscan = nullptr;  // [cap + 1]
+  // merge
+  uint64_t* prefix = nullptr;  // [4][cap + 1]: sum k, sum k ux, uy, uz
+  int32_t* mend = nullptr;     // [cap]
+  // tree
+  Node* nodes = nullptr;
+  int32_t* lvl_count = nullptr;  // [kMaxLevel + 2]
+  uint64_t* nsum = nullptr;      // [3][node cap] scratch sums
+  int32_t* groups = nullptr;     // [cap]
+  int32_t* group_head = nullptr; // [cap]
+  // PM
+  void* rho = nullptr;    // real [M^3]
+  void* spec = nullptr;   // cplx [M][M][M/2+1]
+  void* phi = nullptr;    // real [M^3]
+  int32_t* cell_start = nullptr;  // [M^3 + 1]
+  void* twiddle = nullptr;        // cplx tables
+  void* green_axis = nullptr;     // per-axis Green factors
+  // lightcone ring
+  dzs_lc_record* ring = nullptr;
+  // device scalars
+  int32_t* n = nullptr;          // particle count
+  uint32_t* err = nullptr;       // error word
+  // [16]: 0 ring head, 1 records dropped, 2 groups, 3 nodes, 4 pair evaluations,
+  // 6 walk work counter, 8..11 diagnostics integer sums
+  uint64_t* counters = nullptr;
+  double* diag = nullptr;        // [8 + blocks] diagnostics partials
+  void* convert = nullptr;       // double [3][cap] conversion scratch
+};
+
+}  // namespace dzs
+
+struct dzs_ctx {
+  dzs_params P;
+  int dev = 0;
+  cudaStream_t stream = nullptr;
+  bool fp64 = false;
+  int64_t N0 = 0, cap = 0, node_cap = 0;
+  int M = 0, logM = 0, n1 = 0;
+  int sort_blocks = 0;
+  double lat = 0, scale = 0, gm0 = 0, eps0 = 0, rs = 0, rcut = 0, rcut_lat2 = 0;
+  int jmin = 1;
+  uint64_t blat = 0;
+  uint64_t merge_thr[dzs::kMaxLevel + 1];
+  dzs::Tables T;
+  int32_t step = 0;
+  bool have_state = false;
+  bool poisoned = false;
+  uint64_t drained = 0;
+  size_t ring_cap = 0;
+  char* arena = nullptr;
+  size_t arena_bytes = 0;
+  dzs::Buffers B;
+  std::string err;
+  uint64_t launches = 0;  // kernels launched (host-side count)
+  // per-stage CUDA-event profiling
+  bool prof_on = false;
+  struct ProfEv {
+    int cat;
+    cudaEvent_t a, b;
+  };
+  std::vector<ProfEv> prof_pending;
+  std::vector<cudaEvent_t> ev_pool;
+  double prof_ms[8] = {0};
+  uint64_t prof_calls[8] = {0};
+};
+
+namespace dzs {
+
+// host-side cosmology (host.cu)
+void compute_tables(const dzs_params& P, Tables& T);
+double bbks_shape(const dzs_params& P, double k);  // k^ns T(k)^2
+
+// launchers (each file); all enqueue on c->stream
+void launch_kick_drift(dzs_ctx* c, int step, bool kick, bool drift);
+void launch_records(dzs_ctx* c, int step);
+void launch_sort(dzs_ctx* c);
+void launch_keys(dzs_ctx* c);
+void launch_unpermute(dzs_ctx* c, double* g_out);
+void launch_close_kick(dzs_ctx* c, int step);
+void launch_merge(dzs_ctx* c, uint64_t rlat);
+void launch_tree(dzs_ctx* c);
+void launch_pm(dzs_ctx* c, bool want_pm);
+void launch_walk(dzs_ctx* c, bool tree, bool close_kick, int step);
+void launch_diagnostics(dzs_ctx* c);
+void launch_ics(dzs_ctx* c);
+void launch_to_double(dzs_ctx* c, const void* src, int64_t count, double* dst);
+void launch_from_double(dzs_ctx* c, const double* src, int64_t count, void* dst);
+void launch_fft_init(dzs_ctx* c);
+template <class R>
+void fft_r2c_3d(dzs_ctx* c, const R* in, cplx<R>* out, int n, const cplx<R>* tw);
+template <class R>
+void fft_c2r_3d(dzs_ctx* c, cplx<R>* in, R* out, int n, const cplx<R>* tw, const R* green, R gfac);
+
+// deterministic exclusive scan of int32 flags/counts -> iscan[0..n], n on device
+void exclusive_scan_i32(dzs_ctx* c, const int32_t* in, int32_t* out, const int32_t* d_n, int64_t cap);
+
+}  // namespace dzs

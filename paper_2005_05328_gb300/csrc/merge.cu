@@ -1,0 +1,265 @@
+// merge.cu -- the DZS de-refinement (paper Sec. 2.2, Fig. 2; Eq. 3;
+// Sec. 2.2.1 geometric criterion with the l_max limit).
+//
+// GPU formulation of the top-down walk: every octree cell is a run of the
+// Morton-sorted particles, and its mass and mass-weighted position are exact
+// differences of uint64 prefix sums (masses are integer multiples of m0, so
+// the sums are exact in any order).  Each particle walks its own root-to-leaf
+// path from the coarsest candidate level j_min (side <= l_max), locating its
+// cell by binary search inside the parent's range, and stops at the first
+// cell with >= 2 particles that qualifies:
+//     d_COM^2 > T_j^2,   T_j = R_lat + b_lat + ceil(l_j / theta_dzs),
+// which is l_j / D_n < theta_dzs with D_n = d_COM - R_lc - b (Eq. 3).  Every
+// member reaches the same decision, so the walk needs no synchronisation.
+// The first member of a merged cell becomes the new particle (mass K, integer
+// COM rounded half up, p = (sum k p) / K summed left to right in FP64,
+// id = min id); the others are dropped by a stable compaction.
+#include "common.cuh"
+
+namespace dzs {
+namespace {
+
+constexpr int kChunk = 1024;
+
+struct MergeParams {
+  uint64_t thr[kMaxLevel + 1];  // T_j (UINT64_MAX: level never merges)
+  uint64_t rb2;                 // (R_lat + b_lat)^2: members must lie beyond
+  int jmin;
+  int filter;                   // 1 when theta_dzs <= 1/sqrt(3)
+};
+
+// ---- 4-channel uint64 exclusive prefix sums: k, k ux, k uy, k uz
+__global__ void k_prefix_totals(const int32_t* __restrict__ d_n, int64_t cap, const uint32_t* __restrict__ u,
+                                const uint32_t* __restrict__ k, uint64_t* __restrict__ tot) {
+  const int64_t n = *d_n;
+  int64_t base = (int64_t)blockIdx.x * kChunk;
+  unsigned long long s[4] = {0, 0, 0, 0};
+  for (int t = threadIdx.x; t < kChunk; t += blockDim.x) {
+    int64_t i = base + t;
+    if (i < n) {
+      uint64_t kk = k[i];
+      s[0] += kk;
+      for (int ax = 0; ax < 3; ++ax) s[1 + ax] += kk * u[ax * cap + i];
+    }
+  }
+  for (int q = 0; q < 4; ++q) {
+    for (int o = 16; o > 0; o >>= 1) s[q] += __shfl_down_sync(0xffffffffu, s[q], o);
+  }
+  __shared__ unsigned long long ws[4][32];
+  if ((threadIdx.x & 31) == 0)
+    for (int q = 0; q < 4; ++q) ws[q][threadIdx.x >> 5] = s[q];
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    unsigned long long a = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += ws[threadIdx.x][w];
+    tot[(int64_t)threadIdx.x * (gridDim.x + 1) + blockIdx.x] = a;
+  }
+}
+
+__global__ void k_prefix_scan_totals(uint64_t* __restrict__ tot, int nchunks) {
+  // one thread per channel: chunks are few (n / 1024)
+  if (threadIdx.x >= 4) return;
+  uint64_t* row = tot + (int64_t)threadIdx.x * (nchunks + 1);
+  uint64_t s = 0;
+  for (int b = 0; b < nchunks; ++b) {
+    uint64_t v = row[b];
+    row[b] = s;
+    s += v;
+  }
+  row[nchunks] = s;
+}
+
+__global__ void k_prefix_apply(const int32_t* __restrict__ d_n, int64_t cap, const uint32_t* __restrict__ u,
+                               const uint32_t* __restrict__ k, const uint64_t* __restrict__ tot, int nchunks,
+                               uint64_t* __restrict__ pre) {
+  const int64_t n = *d_n;
+  int64_t base = (int64_t)blockIdx.x * kChunk;
+  if (base > n) return;
+  // thread t owns items base + 4t .. base + 4t + 3
+  int64_t i0 = base + 4 * threadIdx.x;
+  unsigned long long v[4][4], s[4] = {0, 0, 0, 0};
+  for (int q = 0; q < 4; ++q) {
+    int64_t i = i0 + q;
+    uint64_t kk = (i < n) ? k[i] : 0;
+    v[0][q] = kk;
+    for (int ax = 0; ax < 3; ++ax) v[1 + ax][q] = (i < n) ? kk * u[ax * cap + i] : 0;
+    for (int c = 0; c < 4; ++c) s[c] += v[c][q];
+  }
+  // block exclusive scan per channel (warp shuffles + warp totals)
+  __shared__ unsigned long long wt[4][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  unsigned long long inc[4];
+  for (int c = 0; c < 4; ++c) {
+    inc[c] = s[c];
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned long long t = __shfl_up_sync(0xffffffffu, inc[c], o);
+      if (lane >= o) inc[c] += t;
+    }
+    if (lane == 31) wt[c][w] = inc[c];
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    unsigned long long a = 0;
+    for (int q = 0; q < nw; ++q) {
+      unsigned long long t = wt[threadIdx.x][q];
+      wt[threadIdx.x][q] = a;
+      a += t;
+    }
+  }
+  __syncthreads();
+  for (int c = 0; c < 4; ++c) {
+    unsigned long long run = tot[(int64_t)c * (nchunks + 1) + blockIdx.x] + wt[c][w] + inc[c] - s[c];
+    for (int q = 0; q < 4; ++q) {
+      int64_t i = i0 + q;
+      if (i <= n) pre[(int64_t)c * (cap + 1) + i] = run;
+      run += v[c][q];
+    }
+  }
+}
+
+__device__ __forceinline__ int64_t lower_bound_key(const uint64_t* __restrict__ key, int64_t lo, int64_t hi,
+                                                   uint64_t x) {
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if (key[mid] < x)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// mend[i]: end of the merged run if i leads one, -1 if i is merged away, 0 if kept
+__global__ void k_merge_mark(const int32_t* __restrict__ d_n, int64_t cap, const uint64_t* __restrict__ key,
+                             const uint32_t* __restrict__ u, const uint64_t* __restrict__ pre,
+                             int32_t* __restrict__ mend, int32_t* __restrict__ keep, MergeParams mp) {
+  const int64_t n = *d_n;
+  const uint64_t* PK = pre;
+  const uint64_t* PS = pre + (cap + 1);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    int32_t res = 0;
+    bool cand = true;
+    if (mp.filter) cand = dist2_obs(u[i], u[cap + i], u[2 * cap + i]) > mp.rb2;
+    if (cand) {
+      uint64_t ki = key[i];
+      int64_t lo = 0, hi = n;
+      for (int j = 1; j <= kMaxLevel; ++j) {
+        int sh = 3 * (kMaxLevel - j);
+        uint64_t cell = (ki >> sh) << sh;
+        int64_t s = lower_bound_key(key, lo, i + 1, cell);
+        int64_t e = lower_bound_key(key, i + 1, hi, cell + (1ull << sh));
+        lo = s;
+        hi = e;
+        if (e - s < 2) break;  // no finer cell holds two particles
+        if (j < mp.jmin || mp.thr[j] == ~0ull) continue;
+        uint64_t K = PK[e] - PK[s];
+        uint64_t d2 = 0;
+        for (int ax = 0; ax < 3; ++ax) {
+          uint64_t S = PS[(int64_t)ax * (cap + 1) + e] - PS[(int64_t)ax * (cap + 1) + s];
+          uint32_t com = (uint32_t)((2 * S + K) / (2 * K));
+          int64_t off = (int32_t)(com - 0x80000000u);
+          d2 += (uint64_t)(off * off);
+        }
+        uint64_t T = mp.thr[j];
+        if (d2 > T * T) {
+          res = (s == i) ? (int32_t)e : -1;
+          break;
+        }
+      }
+    }
+    mend[i] = res;
+    keep[i] = res >= 0 ? 1 : 0;
+  }
+}
+
+template <class R>
+__global__ void k_merge_write(const int32_t* __restrict__ d_n, int64_t cap, const int32_t* __restrict__ mend,
+                              const int32_t* __restrict__ rank, const uint64_t* __restrict__ key,
+                              const uint32_t* __restrict__ u, const R* __restrict__ p,
+                              const uint32_t* __restrict__ k, const uint32_t* __restrict__ id,
+                              const uint8_t* __restrict__ fl, const uint64_t* __restrict__ pre,
+                              uint64_t* __restrict__ key2, uint32_t* __restrict__ u2, R* __restrict__ p2,
+                              uint32_t* __restrict__ k2, uint32_t* __restrict__ id2, uint8_t* __restrict__ fl2,
+                              int32_t* __restrict__ d_n_out) {
+  const int64_t n = *d_n;
+  const uint64_t* PK = pre;
+  const uint64_t* PS = pre + (cap + 1);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    int32_t m = mend[i];
+    if (m < 0) continue;
+    int64_t j = rank[i];
+    if (m == 0) {
+      for (int ax = 0; ax < 3; ++ax) {
+        u2[ax * cap + j] = u[ax * cap + i];
+        p2[ax * cap + j] = p[ax * cap + i];
+      }
+      key2[j] = key[i];
+      k2[j] = k[i];
+      id2[j] = id[i];
+      fl2[j] = fl[i];
+      continue;
+    }
+    int64_t e = m;
+    uint64_t K = PK[e] - PK[i];
+    uint32_t com[3];
+    for (int ax = 0; ax < 3; ++ax) {
+      uint64_t S = PS[(int64_t)ax * (cap + 1) + e] - PS[(int64_t)ax * (cap + 1) + i];
+      com[ax] = (uint32_t)((2 * S + K) / (2 * K));
+      double acc = 0.0;  // left-to-right FP64 sum, no contraction
+      for (int64_t t = i; t < e; ++t) acc = __dadd_rn(acc, __dmul_rn((double)k[t], (double)p[ax * cap + t]));
+      u2[ax * cap + j] = com[ax];
+      p2[ax * cap + j] = (R)(acc / (double)K);
+    }
+    uint32_t idm = id[i];
+    for (int64_t t = i + 1; t < e; ++t) idm = min(idm, id[t]);
+    key2[j] = morton_key(com[0], com[1], com[2]);
+    k2[j] = (uint32_t)K;
+    id2[j] = idm;
+    fl2[j] = (uint8_t)(kFlMerged | kFlCrossed);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *d_n_out = rank[n];
+}
+
+}  // namespace
+
+void launch_merge(dzs_ctx* c, uint64_t rlat) {
+  c->launches += 8;
+  Buffers& B = c->B;
+  MergeParams mp;
+  for (int j = 0; j <= kMaxLevel; ++j)
+    mp.thr[j] = (c->merge_thr[j] == ~0ull) ? ~0ull : rlat + c->merge_thr[j];
+  for (int j = 0; j <= kMaxLevel; ++j)
+    if (mp.thr[j] != ~0ull && mp.thr[j] >= 4294967296ull) mp.thr[j] = ~0ull;
+  uint64_t rb = rlat + c->blat;
+  mp.rb2 = (rb >= 4294967296ull) ? ~0ull : rb * rb;
+  mp.jmin = c->jmin;
+  mp.filter = (c->P.theta_dzs <= 0.5773502691896257) ? 1 : 0;
+  int nchunks = (int)((c->cap + kChunk) / kChunk);
+  uint64_t* tot = (uint64_t*)B.blocksum;
+  k_prefix_totals<<<nchunks, 256, 0, c->stream>>>(B.n, c->cap, B.u, B.k, tot);
+  k_prefix_scan_totals<<<1, 32, 0, c->stream>>>(tot, nchunks);
+  k_prefix_apply<<<nchunks, 256, 0, c->stream>>>(B.n, c->cap, B.u, B.k, tot, nchunks, B.prefix);
+  int32_t* keep = B.iscan + (c->cap + 1);
+  int32_t* rank = B.iscan;
+  int grid = grid_for(c->N0);
+  k_merge_mark<<<grid, kThreads, 0, c->stream>>>(B.n, c->cap, B.key, B.u, B.prefix, B.mend, keep, mp);
+  exclusive_scan_i32(c, keep, rank, B.n, c->cap);
+  if (c->fp64)
+    k_merge_write<double><<<grid, kThreads, 0, c->stream>>>(
+        B.n, c->cap, B.mend, rank, B.key, B.u, (const double*)B.p, B.k, B.id, B.fl, B.prefix, B.key2, B.u2,
+        (double*)B.p2, B.k2, B.id2, B.fl2, B.n + 1);
+  else
+    k_merge_write<float><<<grid, kThreads, 0, c->stream>>>(
+        B.n, c->cap, B.mend, rank, B.key, B.u, (const float*)B.p, B.k, B.id, B.fl, B.prefix, B.key2, B.u2,
+        (float*)B.p2, B.k2, B.id2, B.fl2, B.n + 1);
+  // new count staged in n[1] (every thread of the write kernel read n[0])
+  cudaMemcpyAsync(B.n, B.n + 1, sizeof(int32_t), cudaMemcpyDeviceToDevice, c->stream);
+  std::swap(B.key, B.key2);
+  std::swap(B.u, B.u2);
+  std::swap(B.p, B.p2);
+  std::swap(B.k, B.k2);
+  std::swap(B.id, B.id2);
+  std::swap(B.fl, B.fl2);
+}
+
+}  // namespace dzs

@@ -1,0 +1,265 @@
+// sort.cu -- stable LSD radix sort of the 63-bit Morton keys (8-bit digits,
+// 8 passes) carrying the particle index, then one gather pass that permutes
+// the particle state into Morton order.
+//
+// The oct-tree of the paper (Sec. 2.1) becomes an implicit octree over the
+// sorted keys: every octree cell is a contiguous run of the sorted array.
+// Each pass: per-tile digit histograms, a per-digit scan over tiles, and a
+// stable scatter (rank = earlier items of the same digit in the tile).  Ties
+// keep the previous order, so the result is deterministic.
+#include "common.cuh"
+
+namespace dzs {
+namespace {
+
+constexpr int kSortThreads = 256;
+constexpr int kItems = 8;
+constexpr int kTile = kSortThreads * kItems;  // 2048 keys per block
+constexpr int kDigits = 256;
+
+__global__ void k_hist(const uint64_t* __restrict__ key, const int32_t* __restrict__ d_n, int shift,
+                       uint32_t* __restrict__ hist, int nb) {
+  __shared__ uint32_t cnt[kDigits];
+  cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t n = *d_n;
+  int64_t base = (int64_t)blockIdx.x * kTile;
+  for (int s = 0; s < kItems; ++s) {
+    int64_t i = base + s * kSortThreads + threadIdx.x;
+    if (i < n) atomicAdd(&cnt[(key[i] >> shift) & 0xff], 1u);
+  }
+  __syncthreads();
+  hist[threadIdx.x * nb + blockIdx.x] = cnt[threadIdx.x];
+}
+
+// block d: exclusive scan of row d of the histogram, row total to rowtot[d]
+__global__ void k_scan_rows(uint32_t* __restrict__ hist, int nb, uint32_t* __restrict__ rowtot) {
+  __shared__ uint32_t warp_tot[32];
+  __shared__ uint32_t carry;
+  uint32_t* row = hist + (int64_t)blockIdx.x * nb;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int b0 = 0; b0 < nb; b0 += blockDim.x) {
+    int b = b0 + threadIdx.x;
+    uint32_t v = b < nb ? row[b] : 0u, inc = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += t;
+    }
+    if (lane == 31) warp_tot[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+      uint32_t t = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0u, ti = t;
+      for (int o = 1; o < 32; o <<= 1) {
+        uint32_t q = __shfl_up_sync(0xffffffffu, ti, o);
+        if (lane >= o) ti += q;
+      }
+      warp_tot[lane] = ti - t;
+    }
+    __syncthreads();
+    uint32_t ex = inc - v + warp_tot[w] + carry;
+    if (b < nb) row[b] = ex;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry = ex + v;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) rowtot[blockIdx.x] = carry;
+}
+
+__global__ void k_scatter(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                          uint64_t* __restrict__ kout, uint32_t* __restrict__ vout,
+                          const int32_t* __restrict__ d_n, int shift, const uint32_t* __restrict__ hist,
+                          int nb, const uint32_t* __restrict__ rowtot, bool identity_values) {
+  __shared__ uint32_t gbase[kDigits];
+  __shared__ uint32_t run[kDigits];
+  __shared__ uint32_t wcnt[kSortThreads / 32][kDigits];
+  const int64_t n = *d_n;
+  int64_t base = (int64_t)blockIdx.x * kTile;
+  if (base >= n) return;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  // digit bases: exclusive scan of the 256 row totals (thread t owns digit t)
+  {
+    __shared__ uint32_t tot[kDigits];
+    tot[t] = rowtot[t];
+    __syncthreads();
+    if (t == 0) {
+      uint32_t s = 0;
+      for (int d = 0; d < kDigits; ++d) {
+        uint32_t v = tot[d];
+        tot[d] = s;
+        s += v;
+      }
+    }
+    __syncthreads();
+    gbase[t] = tot[t] + hist[(int64_t)t * nb + blockIdx.x];
+    run[t] = 0;
+  }
+  __syncthreads();
+  const unsigned lt = (1u << lane) - 1u;
+  for (int s = 0; s < kItems; ++s) {
+    for (int q = 0; q < kSortThreads / 32; ++q) wcnt[q][t] = 0;
+    __syncthreads();
+    int64_t i = base + s * kSortThreads + t;
+    bool valid = i < n;
+    uint64_t kv = valid ? kin[i] : 0ull;
+    uint32_t vv = valid ? (identity_values ? (uint32_t)i : vin[i]) : 0u;
+    int d = valid ? (int)((kv >> shift) & 0xff) : kDigits;  // invalid items group apart
+    unsigned peers = __match_any_sync(0xffffffffu, d);
+    int rank_w = __popc(peers & lt);
+    if (valid && rank_w == 0) wcnt[w][d] = __popc(peers);
+    __syncthreads();
+    {
+      uint32_t off = run[t];
+      for (int q = 0; q < kSortThreads / 32; ++q) {
+        uint32_t c = wcnt[q][t];
+        wcnt[q][t] = off;
+        off += c;
+      }
+      run[t] = off;
+    }
+    __syncthreads();
+    if (valid) {
+      uint32_t pos = gbase[d] + wcnt[w][d] + (uint32_t)rank_w;
+      kout[pos] = kv;
+      vout[pos] = vv;
+    }
+    __syncthreads();
+  }
+}
+
+template <class R>
+__global__ void k_permute(const int32_t* __restrict__ d_n, int64_t cap, const uint32_t* __restrict__ idx,
+                          const uint32_t* __restrict__ u, const R* __restrict__ p,
+                          const uint32_t* __restrict__ k, const uint32_t* __restrict__ id,
+                          const uint8_t* __restrict__ fl, uint32_t* __restrict__ u2, R* __restrict__ p2,
+                          uint32_t* __restrict__ k2, uint32_t* __restrict__ id2, uint8_t* __restrict__ fl2) {
+  const int64_t n = *d_n;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    int64_t s = idx[t];
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+      u2[ax * cap + t] = u[ax * cap + s];
+      p2[ax * cap + t] = p[ax * cap + s];
+    }
+    k2[t] = k[s];
+    id2[t] = id[s];
+    fl2[t] = fl[s];
+  }
+}
+
+}  // namespace
+
+void launch_sort(dzs_ctx* c) {
+  c->launches += 25;
+  Buffers& B = c->B;
+  int nb = (int)((c->cap + kTile - 1) / kTile);
+  uint32_t* rowtot = B.hist + (int64_t)kDigits * nb;
+  uint64_t *kin = B.key, *kout = B.key2;
+  uint32_t *vin = B.idx, *vout = B.idx2;
+  for (int pass = 0; pass < 8; ++pass) {
+    int shift = 8 * pass;
+    k_hist<<<nb, kSortThreads, 0, c->stream>>>(kin, B.n, shift, B.hist, nb);
+    k_scan_rows<<<kDigits, 1024, 0, c->stream>>>(B.hist, nb, rowtot);
+    k_scatter<<<nb, kSortThreads, 0, c->stream>>>(kin, vin, kout, vout, B.n, shift, B.hist, nb, rowtot,
+                                                  pass == 0);
+    std::swap(kin, kout);
+    std::swap(vin, vout);
+  }
+  // 8 passes: sorted keys and indices are back in key / idx
+  int grid = grid_for(c->N0);
+  if (c->fp64)
+    k_permute<double><<<grid, kThreads, 0, c->stream>>>(B.n, c->cap, B.idx, B.u, (const double*)B.p, B.k, B.id,
+                                                        B.fl, B.u2, (double*)B.p2, B.k2, B.id2, B.fl2);
+  else
+    k_permute<float><<<grid, kThreads, 0, c->stream>>>(B.n, c->cap, B.idx, B.u, (const float*)B.p, B.k, B.id,
+                                                       B.fl, B.u2, (float*)B.p2, B.k2, B.id2, B.fl2);
+  std::swap(B.u, B.u2);
+  std::swap(B.p, B.p2);
+  std::swap(B.k, B.k2);
+  std::swap(B.id, B.id2);
+  std::swap(B.fl, B.fl2);
+}
+
+}  // namespace dzs
+
+// ---- helpers used by the state-injection entry points
+
+namespace dzs {
+namespace {
+
+__global__ void k_keys(const int32_t* __restrict__ d_n, int64_t cap, const uint32_t* __restrict__ u,
+                       uint64_t* __restrict__ key) {
+  const int64_t n = *d_n;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    key[i] = morton_key(u[i], u[cap + i], u[2 * cap + i]);
+}
+
+// undo the last sort: sorted slot t goes back to idx[t]; g (sorted) is written
+// as double in the original order with stride n
+template <class R>
+__global__ void k_unpermute(const int32_t* __restrict__ d_n, int64_t cap, const uint32_t* __restrict__ idx,
+                            const uint32_t* __restrict__ u, const R* __restrict__ p, const R* __restrict__ g,
+                            const uint32_t* __restrict__ k, const uint32_t* __restrict__ id,
+                            const uint8_t* __restrict__ fl, uint32_t* __restrict__ u2, R* __restrict__ p2,
+                            uint32_t* __restrict__ k2, uint32_t* __restrict__ id2, uint8_t* __restrict__ fl2,
+                            double* __restrict__ gout) {
+  const int64_t n = *d_n;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    int64_t o = idx[t];
+    for (int ax = 0; ax < 3; ++ax) {
+      u2[ax * cap + o] = u[ax * cap + t];
+      p2[ax * cap + o] = p[ax * cap + t];
+      gout[ax * n + o] = (double)g[ax * cap + t];
+    }
+    k2[o] = k[t];
+    id2[o] = id[t];
+    fl2[o] = fl[t];
+  }
+}
+
+template <class R>
+__global__ void k_close_kick(const int32_t* __restrict__ d_n, int64_t cap, R* __restrict__ p,
+                             const R* __restrict__ g, R kick) {
+  const int64_t n = *d_n;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    for (int ax = 0; ax < 3; ++ax) p[ax * cap + i] += g[ax * cap + i] * kick;
+}
+
+}  // namespace
+
+void launch_keys(dzs_ctx* c) {
+  c->launches += 1;
+  k_keys<<<grid_for(c->N0), kThreads, 0, c->stream>>>(c->B.n, c->cap, c->B.u, c->B.key);
+}
+
+void launch_unpermute(dzs_ctx* c, double* g_out) {
+  c->launches += 1;
+  Buffers& B = c->B;
+  int grid = grid_for(c->N0);
+  if (c->fp64)
+    k_unpermute<double><<<grid, kThreads, 0, c->stream>>>(B.n, c->cap, B.idx, B.u, (const double*)B.p,
+                                                          (const double*)B.g, B.k, B.id, B.fl, B.u2,
+                                                          (double*)B.p2, B.k2, B.id2, B.fl2, g_out);
+  else
+    k_unpermute<float><<<grid, kThreads, 0, c->stream>>>(B.n, c->cap, B.idx, B.u, (const float*)B.p,
+                                                         (const float*)B.g, B.k, B.id, B.fl, B.u2, (float*)B.p2,
+                                                         B.k2, B.id2, B.fl2, g_out);
+  std::swap(B.u, B.u2);
+  std::swap(B.p, B.p2);
+  std::swap(B.k, B.k2);
+  std::swap(B.id, B.id2);
+  std::swap(B.fl, B.fl2);
+}
+
+void launch_close_kick(dzs_ctx* c, int step) {
+  c->launches += 1;
+  if (c->fp64)
+    k_close_kick<double><<<grid_for(c->N0), kThreads, 0, c->stream>>>(c->B.n, c->cap, (double*)c->B.p,
+                                                                      (const double*)c->B.g, c->T.kick2[step]);
+  else
+    k_close_kick<float><<<grid_for(c->N0), kThreads, 0, c->stream>>>(c->B.n, c->cap, (float*)c->B.p,
+                                                                     (const float*)c->B.g, (float)c->T.kick2[step]);
+}
+
+}  // namespace dzs
