@@ -23,20 +23,21 @@ __device__ __forceinline__ int32_t warp_incl_scan(int32_t v) {
 
 // block-wide exclusive scan of one value per thread; returns the block total
 __device__ int32_t block_excl_scan(int32_t v, int32_t* excl) {
-  __shared__ int32_t warp_tot[32];
+  __shared__ int32_t warp_off[32];
+  __shared__ int32_t block_total;  // separate slot: a 1024-thread block uses all 32 offsets
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   int32_t inc = warp_incl_scan(v);
-  if (lane == 31) warp_tot[w] = inc;
+  if (lane == 31) warp_off[w] = inc;
   __syncthreads();
   if (w == 0) {
-    int32_t t = lane < nw ? warp_tot[lane] : 0;
+    int32_t t = lane < nw ? warp_off[lane] : 0;
     int32_t ti = warp_incl_scan(t);
-    if (lane < nw) warp_tot[lane] = ti - t;
-    if (lane == nw - 1) warp_tot[31] = ti;
+    if (lane < nw) warp_off[lane] = ti - t;
+    if (lane == nw - 1) block_total = ti;
   }
   __syncthreads();
-  *excl = inc - v + warp_tot[w];
-  int32_t total = warp_tot[31];
+  *excl = inc - v + warp_off[w];
+  int32_t total = block_total;
   __syncthreads();
   return total;
 }

@@ -1,0 +1,98 @@
+"""Parity at the benchmark's full size (128^3 particles, L = 256 Mpc/h, mesh
+256^3, the launch configuration bench.py times): sampled accelerations the
+oracle computes one by one, a bit-exact full-size merge, and properties that
+hold at any size over GPU-only steps.
+
+The input is the oracle's own Zel'dovich field with sigma8 = 2.5 (strongly
+non-linear displacements: caustics, deep trees, long interaction lists) and
+seeded random multiplicities k in [1, 8] (varying masses and softenings)."""
+import numpy as np
+import pytest
+
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+TWO32 = 2 ** 32
+KW = dict(n1d=128, mesh=256, box=256.0, merge_level=3, sigma8=2.5, seed=5)
+
+
+@pytest.fixture(scope="module")
+def dzs():
+    from paper_2005_05328_gb300 import build
+    build.build()
+    import paper_2005_05328_gb300 as m
+    m.load()
+    return m
+
+
+@pytest.fixture(scope="module")
+def state():
+    P = O.params(**KW)
+    st = O.ics(P)
+    key, perm = O.sort(st["u"])
+    n = st["u"].shape[1]
+    rng = np.random.default_rng(11)
+    k = rng.integers(1, 9, size=n).astype(np.uint32)
+    return P, dict(u=st["u"][:, perm].copy(), p=st["p"][:, perm].copy(), k=k,
+                   id=st["id"][perm].copy(), fl=np.zeros(n, np.uint8))
+
+
+def rel_err(got, want):
+    err = np.linalg.norm(got - want, axis=0)
+    ref = np.linalg.norm(want, axis=0)
+    rms = np.sqrt((ref ** 2).mean())
+    return err / (ref + 1e-3 * rms)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_accel_sampled(dzs, state, precision):
+    P, st = state
+    n = st["u"].shape[1]
+    rng = np.random.default_rng(1)
+    sample = np.sort(rng.choice(n, 3000, replace=False))
+    want = O.accel(P, st["u"], st["k"], sample=sample)[:, sample]
+    with dzs.Context(**KW, precision=precision) as ctx:
+        ctx.set_state(dict(st, g=np.zeros((3, n))), 0)
+        got = ctx.accel()[:, sample]
+        cnt = ctx.counters()
+    assert cnt[3] == 0  # no device buffer overflow
+    e = rel_err(got, want)
+    if precision == 1:
+        assert e.max() <= 1e-9, e.max()
+    else:
+        assert np.percentile(e, 99.9) <= 1e-4, (np.percentile(e, 99.9), e.max())
+
+
+def test_merge_full_size_bit_exact(dzs, state):
+    P, st = state
+    st = dict(st, fl=np.full(st["u"].shape[1], O.FL_CROSSED, np.uint8))
+    rlat = int(0.25 * TWO32)
+    want = O.merge(P, rlat, st)
+    assert want["u"].shape[1] < st["u"].shape[1] // 2
+    with dzs.Context(**KW, precision=1) as ctx:
+        ctx.set_state(dict(st, g=np.zeros_like(st["p"])), 0)
+        ctx.merge_only(rlat)
+        got = ctx.state()
+    for name in ("u", "k", "id", "fl", "p"):
+        assert np.array_equal(got[name], want[name]), name
+
+
+def test_gpu_run_invariants(dzs):
+    kw = dict(n1d=128, mesh=256, box=256.0, merge_level=3, seed=2)
+    with dzs.Context(**kw) as ctx:
+        ctx.ics()
+        n0 = 128 ** 3
+        seen = []
+        for _ in range(4):
+            ctx.step(24)
+            seen.append(ctx.drain(cap=n0)["id"])
+            d = ctx.diagnostics()
+            assert d[0] == n0
+        n, step = ctx.count()
+        cnt = ctx.counters()
+    ids = np.concatenate(seen)
+    assert step == 96
+    assert len(ids) == n0 and len(np.unique(ids)) == n0
+    assert n < n0 // 4  # most of the box ends outside the lightcone and is merged
+    assert cnt[3] == 0

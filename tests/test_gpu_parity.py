@@ -234,7 +234,16 @@ def test_kick_drift_records(dzs, precision):
         s = ctx.state()
         r = ctx.drain()
     du = (s["u"].astype(np.int64) - so["u"].astype(np.int64) + 2 ** 31) % TWO32 - 2 ** 31
-    assert np.abs(du).max() <= 1
+    if precision == 1:
+        assert np.abs(du).max() <= 1
+    else:
+        # FP32 kick: the kicked momentum is rounded to float (relative 2^-24 per
+        # operation) before the FP64 drift product, so the lattice step can
+        # differ by a few units: |du| <= 1 + 3e-7 (|p| + |g K1|) D 2^32 / L
+        T = O.tables(P)
+        dlat = T["drift"][60] * TWO32 / P.box
+        bound = 1 + 3e-7 * (np.abs(st["p"]) + np.abs(st["g"] * T["kick1"][60])) * dlat
+        assert np.all(np.abs(du) <= bound)
     assert np.array_equal(np.sort(r["id"]), np.sort(rec["id"]))
     assert np.array_equal(s["fl"], so["fl"])
     ro, rg = rec[np.argsort(rec["id"])], r[np.argsort(r["id"])]
