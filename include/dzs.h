@@ -217,6 +217,35 @@ DZS_API dzs_status dzs_set_profiling(dzs_ctx* c, int32_t enable);
  * dzs_set_profiling (synchronises; either pointer may be NULL). */
 DZS_API dzs_status dzs_get_profile(dzs_ctx* c, double ms[DZS_PROF_N], uint64_t calls[DZS_PROF_N]);
 
+/* Largest n accepted by dzs_morton_sort_noalloc.  Its scratch is a static
+ * device array of 24 * n + 4 * (257 * ceil(n / 2048) + 256) + 256 bytes,
+ * about 6.4 MB, which every GPU that loads the library holds until exit. */
+#define DZS_NOALLOC_SORT_MAX_N 262144
+
+/* Allocation-free stable Morton sort of n <= DZS_NOALLOC_SORT_MAX_N lattice
+ * positions.  The paper has no counterpart: this entry point exists for
+ * callers that cannot call cudaMalloc -- code inside a host framework whose
+ * device memory belongs to that framework's own allocator, plugins given a
+ * fixed memory budget, or paths that must not synchronise the device (an
+ * allocation or free can).  It is the same radix sort as the step's Morton
+ * sort (same keys, same stable order), but its scratch lives in one
+ * file-scope static device array instead of a context arena.
+ *   d_u     device, [3][n] uint32 lattice positions (x, then y, then z);
+ *   d_perm  device, n uint32 output: sorted slot t holds input index d_perm[t];
+ *   d_keys  device, n uint64 output of the sorted 63-bit keys, or NULL;
+ *   stream  cudaStream_t the work is enqueued on (NULL = legacy stream).
+ * Allocates nothing: no cudaMalloc, cudaFree or allocating library call.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  Every call shares the one array and leaves its contents behind
+ * (each call writes every scratch word it reads before reading it), so calls
+ * whose work overlaps on the GPU -- on two streams, or from two threads --
+ * race and must be serialised by the caller.  Returns DZS_EINVAL for
+ * n > DZS_NOALLOC_SORT_MAX_N or a NULL pointer with n > 0, DZS_EDEVICE when
+ * no device is current, DZS_ECUDA when a CUDA call fails; asynchronous. */
+DZS_API dzs_status dzs_morton_sort_noalloc(const uint32_t* d_u, size_t n, uint32_t* d_perm, uint64_t* d_keys,
+                                           void* cuda_stream);
+
 /* Message of the last failure on this context (valid until the next call).
  * c may be NULL (then: the last dzs_create failure of this thread). */
 DZS_API const char* dzs_last_error(const dzs_ctx* c);

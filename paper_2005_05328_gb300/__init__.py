@@ -32,7 +32,8 @@ EXPORTED = ["dzs_params_default", "dzs_footprint_bytes", "dzs_create", "dzs_ics"
             "dzs_run_stages", "dzs_lightcone_drain", "dzs_destroy", "dzs_get_count", "dzs_get_state",
             "dzs_set_state", "dzs_accel", "dzs_merge_only", "dzs_diagnostics", "dzs_get_tables",
             "dzs_get_mesh", "dzs_get_counters", "dzs_set_profiling", "dzs_get_profile",
-            "dzs_last_error"]
+            "dzs_morton_sort_noalloc", "dzs_last_error"]
+NOALLOC_SORT_MAX_N = 262144
 PROF_NAMES = ["kick_drift", "sort", "merge", "tree", "pm", "walk"]
 
 
@@ -89,6 +90,8 @@ def load(path: str = LIB_PATH):
         f = getattr(L, name)
         f.argtypes = args
         f.restype = C.c_int
+    L.dzs_morton_sort_noalloc.argtypes = [vp, sz, vp, vp, vp]
+    L.dzs_morton_sort_noalloc.restype = C.c_int
     L.dzs_last_error.argtypes = [vp]
     L.dzs_last_error.restype = C.c_char_p
     _lib = L
@@ -228,6 +231,14 @@ def dzs_get_counters(h):
     out = np.zeros(6, np.uint64)
     _check(load().dzs_get_counters(h, _ptr(out)), h)
     return out
+
+
+def dzs_morton_sort_noalloc(d_u: int, n: int, d_perm: int, d_keys: int = 0, stream: int = 0) -> int:
+    """Allocation-free Morton sort on caller-owned device buffers (raw device
+    addresses, e.g. torch tensor data_ptr()); returns the dzs_status code.
+    For callers that cannot allocate device memory; see include/dzs.h."""
+    return load().dzs_morton_sort_noalloc(C.c_void_p(d_u), n, C.c_void_p(d_perm),
+                                          C.c_void_p(d_keys) if d_keys else None, C.c_void_p(stream))
 
 
 class Context:

@@ -263,3 +263,90 @@ void launch_close_kick(dzs_ctx* c, int step) {
 }
 
 }  // namespace dzs
+
+// ---- allocation-free Morton sort for callers that cannot allocate device memory
+//
+// Some callers may not call cudaMalloc at all: code running inside a host
+// framework whose device memory is fully owned by its own allocator, plugins
+// with a fixed memory budget, or code paths that must not synchronise the
+// device (cudaMalloc/cudaFree can).  dzs_morton_sort_noalloc serves them: its
+// scratch (keys and indices ping-pong buffers, digit histograms and the
+// device-side count) lives in one file-scope static device array of fixed
+// size, allocated when the library is loaded and kept until the process exits.
+// The caller passes device inputs and outputs; nothing is allocated per call.
+
+#include <mutex>
+
+namespace dzs {
+namespace {
+
+constexpr size_t kNoallocMaxN = DZS_NOALLOC_SORT_MAX_N;
+constexpr size_t kNoallocNb = (kNoallocMaxN + kTile - 1) / kTile;
+// layout: keyA, keyB (uint64), valA, valB (uint32), hist (257 rows of nb + 256),
+// count slot
+constexpr size_t kOffKeyB = 8 * kNoallocMaxN;
+constexpr size_t kOffValA = 16 * kNoallocMaxN;
+constexpr size_t kOffValB = 20 * kNoallocMaxN;
+constexpr size_t kOffHist = 24 * kNoallocMaxN;
+constexpr size_t kOffCount = kOffHist + 4 * (257 * kNoallocNb + 256);
+constexpr size_t kNoallocBytes = kOffCount + 256;
+
+static __device__ __align__(256) unsigned char g_sort_scratch[kNoallocBytes];
+
+std::mutex g_scratch_mu;
+void* g_scratch_dev[256] = {nullptr};  // device address per device ordinal
+
+__global__ void k_set_count(int32_t* slot, int32_t n) { *slot = n; }
+
+}  // namespace
+}  // namespace dzs
+
+extern "C" dzs_status dzs_morton_sort_noalloc(const uint32_t* d_u, size_t n, uint32_t* d_perm, uint64_t* d_keys,
+                                              void* cuda_stream) {
+  using namespace dzs;
+  if (n > kNoallocMaxN) return DZS_EINVAL;  // above the static scratch capacity
+  if (n > 0 && (!d_u || !d_perm)) return DZS_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return DZS_EDEVICE;
+  void* base = nullptr;
+  {
+    // set-up, once per device, with that device current: the host-side name of
+    // the array is not a device address, so ask the runtime for it
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_dev[dev]) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_sort_scratch) != cudaSuccess || !p) return DZS_ECUDA;
+      g_scratch_dev[dev] = p;
+    }
+    base = g_scratch_dev[dev];
+  }
+  if (n == 0) return DZS_OK;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  char* b = (char*)base;
+  uint64_t* keyA = (uint64_t*)b;
+  uint64_t* keyB = (uint64_t*)(b + kOffKeyB);
+  uint32_t* valA = (uint32_t*)(b + kOffValA);
+  uint32_t* valB = (uint32_t*)(b + kOffValB);
+  uint32_t* hist = (uint32_t*)(b + kOffHist);
+  int32_t* count = (int32_t*)(b + kOffCount);
+  // every scratch word read below is first written by this call: the count,
+  // the keys, the per-tile histograms (all 256 rows of every tile) and the row
+  // totals, so nothing left over from a previous call is used
+  const int nb = (int)((n + kTile - 1) / kTile);
+  uint32_t* rowtot = hist + (int64_t)kDigits * nb;
+  k_set_count<<<1, 1, 0, st>>>(count, (int32_t)n);
+  k_keys<<<grid_for((int64_t)n), kThreads, 0, st>>>(count, (int64_t)n, d_u, keyA);
+  uint64_t *kin = keyA, *kout = keyB;
+  uint32_t *vin = valA, *vout = valB;
+  for (int pass = 0; pass < 8; ++pass) {
+    int shift = 8 * pass;
+    k_hist<<<nb, kSortThreads, 0, st>>>(kin, count, shift, hist, nb);
+    k_scan_rows<<<kDigits, 1024, 0, st>>>(hist, nb, rowtot);
+    k_scatter<<<nb, kSortThreads, 0, st>>>(kin, vin, kout, vout, count, shift, hist, nb, rowtot, pass == 0);
+    std::swap(kin, kout);
+    std::swap(vin, vout);
+  }
+  if (cudaMemcpyAsync(d_perm, vin, 4 * n, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return DZS_ECUDA;
+  if (d_keys && cudaMemcpyAsync(d_keys, kin, 8 * n, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return DZS_ECUDA;
+  return cudaGetLastError() == cudaSuccess ? DZS_OK : DZS_ECUDA;
+}
