@@ -47,6 +47,22 @@ const char* validate(const dzs_params* p) {
   return nullptr;
 }
 
+// largest x in [0, 2^64) with pass(x) true, for a predicate that is true on a
+// prefix of the integers (pass(0) must hold)
+template <class F>
+uint64_t largest_passing(F pass) {
+  uint64_t lo = 0, hi = ~0ull;
+  if (pass(hi)) return hi;
+  while (hi - lo > 1) {
+    uint64_t mid = lo + (hi - lo) / 2;
+    if (pass(mid))
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
 struct Layout {
   size_t total = 0;
   size_t take(size_t bytes) {
@@ -288,6 +304,15 @@ dzs_status dzs_create(const dzs_params* p, void* cuda_stream, dzs_ctx** out) {
     // same operation order as the definition r_cut / L * 2^32
     double rcut_lat = p->rcut_rs * c->rs / p->box * 4294967296.0;
     c->rcut_lat2 = rcut_lat * rcut_lat;
+  }
+  // the walk keeps a node when (double)gap2 <= r_cut_lat^2 and opens it when
+  // (double)l >= theta * sqrt((double)dcom2); both are monotone in the integer
+  // squared distance, so each becomes "d2 <= largest d2 that passes"
+  c->walk_skip_d2 = largest_passing([&](uint64_t x) { return (double)x <= c->rcut_lat2; });
+  for (int l = 0; l <= kMaxLevel; ++l) {
+    double side = std::ldexp(1.0, 32 - l);
+    double th = p->theta;
+    c->walk_open_d2[l] = largest_passing([&](uint64_t x) { return side >= th * std::sqrt((double)x); });
   }
   int j = 1;
   while (((int64_t)1 << j) * ((int64_t)1 << (p->merge_level - 1)) < p->n1d) ++j;

@@ -144,6 +144,9 @@ struct dzs_ctx {
   int jmin = 1;
   uint64_t blat = 0;
   uint64_t merge_thr[dzs::kMaxLevel + 1];
+  // exact integer forms of the walk's FP64 skip and open comparisons
+  uint64_t walk_skip_d2 = 0;
+  uint64_t walk_open_d2[dzs::kMaxLevel + 1];
   dzs::Tables T;
   int32_t step = 0;
   bool have_state = false;

@@ -4,18 +4,24 @@
 // fused with the closing kick.
 //
 // One warp per walk group (a node with <= G particles whose parent holds more,
-// or a leaf); lane l owns particle start + l.  The warp walks the tree against
-// the group's cube with a shared-memory stack, up to 32 nodes per round (one
-// per lane):
+// or a leaf).  The warp walks the tree against the group's cube with a
+// shared-memory stack, up to 32 nodes per round (one per lane):
 //   skip   the node's cube is farther than r_cut from the group cube;
 //   open   the cubes touch, or l_n >= theta d(COM_n, group cube);
 //   accept otherwise: the monopole (COM, mass, softening) joins the list.
 // Opened leaves put their particles on the list.  Cube gaps and COM distances
-// are exact integers; the two comparisons use FP64 as the CPU reference does,
-// so both sides build the same interaction set.  The list lives in shared
-// memory and is evaluated by all lanes (each for its own particle) whenever it
-// fills: softened pair force times T(r) = erfc(r / 2 r_s) + r / (r_s sqrt(pi))
-// exp(-r^2 / 4 r_s^2), zero at r = 0 or r >= r_cut.
+// are exact integers.  The FP64 comparisons that define skip and open
+// ((double)gap^2 <= r_cut^2, (double)l >= theta sqrt((double)d^2)) are
+// monotone in the integer d^2, so the host turns each into an exact integer
+// threshold once per context: the walk compares integers only and builds the
+// same interaction set as the CPU reference, with no FP64 in the walk.
+// The list lives in shared memory; when it fills, all 32 lanes evaluate it:
+// a group of c particles gets 32 / next_pow2(c) lanes per particle, each lane
+// summing every S-th entry, combined by a fixed xor-shuffle tree (the result
+// is deterministic).  Pair force: softened 1/r^3 times
+// T(r) = erfc(x) + (2/sqrt(pi)) x exp(-x^2), x = r / 2 r_s, zero at r = 0 and
+// r >= r_cut.  FP32 evaluates T = exp(-x^2) Q(x) with a fitted polynomial
+// (gen_split_poly.py, relative error 3.3e-7); FP64 calls erfc and exp.
 #include <cmath>
 
 #include "common.cuh"
@@ -27,6 +33,13 @@ constexpr int kWarps = 4;
 constexpr int kStack = 1024;
 constexpr int kList = 512;
 
+// Q(t) power-series coefficients, t = 2 x / 2.5 - 1; FP32 rel. error 3.32e-07
+// (generated by gen_split_poly.py)
+__constant__ float kSplitPoly[12] = {1.778296833e+00f, 1.149446721e+00f, 1.668713091e-01f, -9.808575506e-02f,
+                                     5.369898964e-02f, -2.768828264e-02f, 1.372957384e-02f, -6.415871732e-03f,
+                                     2.482135905e-03f, -1.056264300e-03f, 7.980994871e-04f, -3.233674216e-04f};
+constexpr float kSplitXMax = 2.5f;
+
 template <class R>
 struct WalkSmem {
   int32_t stack[kWarps][kStack];
@@ -37,18 +50,19 @@ struct WalkSmem {
 
 template <class R>
 struct WalkConst {
-  R scale;       // L / 2^32
-  R rcut2;       // r_cut^2
-  R inv2rs;      // 1 / (2 r_s)
-  R c1;          // 1 / (r_s sqrt(pi))
-  R gm0;         // G m0
-  R h0;          // 2.8 eps0
-  double rcut_lat2;
-  double theta;
-  R kick;        // closing kick factor (0: none)
+  R scale;  // L / 2^32
+  R rcut2;  // r_cut^2
+  R inv2rs;  // 1 / (2 r_s)
+  R c1;      // 2 / sqrt(pi)
+  R gm0;     // G m0
+  R h0;      // 2.8 eps0
+  R kick;    // closing kick factor
+  uint64_t skip_d2;                   // not skipped iff cube gap^2 <= skip_d2
+  uint64_t open_d2[kMaxLevel + 1];    // opened iff COM distance^2 <= open_d2[level]
   int B;
   int close;
   int tree;
+  int poly;  // FP32: use the fitted split polynomial (x_max <= 2.5)
 };
 
 template <class R>
@@ -60,17 +74,27 @@ __device__ __forceinline__ R spline_fac(R r, R h) {
           (R)(1.0 / 15.0) / (q * q * q)) / h3;
 }
 
-__device__ __forceinline__ float erfc_r(float x) { return erfcf(x); }
-__device__ __forceinline__ double erfc_r(double x) { return erfc(x); }
-__device__ __forceinline__ float exp_r(float x) { return __expf(x); }
-__device__ __forceinline__ double exp_r(double x) { return exp(x); }
+__device__ __forceinline__ float split_factor(float x, int poly) {
+  if (poly) {
+    float t = x * (2.0f / kSplitXMax) - 1.0f;
+    float q = kSplitPoly[11];
+#pragma unroll
+    for (int i = 10; i >= 0; --i) q = fmaf(q, t, kSplitPoly[i]);
+    return __expf(-x * x) * q;
+  }
+  return erfcf(x) + 1.1283791670955126f * x * __expf(-x * x);
+}
+
+__device__ __forceinline__ double split_factor(double x, int) {
+  return erfc(x) + 1.1283791670955126 * x * exp(-x * x);
+}
 
 template <class R>
-__device__ __forceinline__ void eval_list(const WalkSmem<R>& sm, int w, int len, bool active, uint32_t xi,
-                                          uint32_t yi, uint32_t zi, R hi, const WalkConst<R>& C, R& ax,
-                                          R& ay, R& az) {
+__device__ __forceinline__ void eval_list(const WalkSmem<R>& sm, int w, int len, int sub, int S, bool active,
+                                          uint32_t xi, uint32_t yi, uint32_t zi, R hi, const WalkConst<R>& C,
+                                          R& ax, R& ay, R& az) {
   if (!active) return;
-  for (int e = 0; e < len; ++e) {
+  for (int e = sub; e < len; e += S) {
     R dx = (R)(int32_t)(sm.lx[w][e] - xi) * C.scale;
     R dy = (R)(int32_t)(sm.ly[w][e] - yi) * C.scale;
     R dz = (R)(int32_t)(sm.lz[w][e] - zi) * C.scale;
@@ -85,9 +109,7 @@ __device__ __forceinline__ void eval_list(const WalkSmem<R>& sm, int w, int len,
       } else {
         fac = spline_fac(r, h);
       }
-      R x = r * C.inv2rs;
-      R t = erfc_r(x) + r * C.c1 * exp_r(-x * x);
-      R f = sm.lm[w][e] * fac * t;
+      R f = sm.lm[w][e] * fac * split_factor(r * C.inv2rs, C.poly);
       ax += f * dx;
       ay += f * dy;
       az += f * dz;
@@ -117,8 +139,12 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(
     const int glevel = gn.meta & 0xff;
     const int64_t lg = 1ll << (32 - glevel);
     for (int c0 = 0; c0 < gn.count; c0 += 32) {
-      const int64_t i = (int64_t)gn.start + c0 + lane;
-      const bool active = c0 + lane < gn.count;
+      // lanes per particle S = 32 / next_pow2(particles in this chunk)
+      const int cnt = gn.count - c0 < 32 ? gn.count - c0 : 32;
+      const int S = 32 >> (32 - __clz(cnt - 1 > 0 ? cnt - 1 : 0));
+      const int mine = lane / S, sub = lane % S;
+      const int64_t i = (int64_t)gn.start + c0 + mine;
+      const bool active = mine < cnt;
       uint32_t xi = 0, yi = 0, zi = 0;
       R hi = 0;
       if (active) {
@@ -142,26 +168,27 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(
           Node nd;
           if (ni >= 0) {
             nd = nodes[ni];
-            const int64_t ln = 1ll << (32 - (int)(nd.meta & 0xff));
+            const int nlevel = (int)(nd.meta & 0xff);
+            const int64_t ln = 1ll << (32 - nlevel);
             bool touch = true;
             uint64_t dist2 = 0, dcom2 = 0;
             const uint32_t cn[3] = {nd.cx, nd.cy, nd.cz}, cg[3] = {gn.cx, gn.cy, gn.cz};
             const uint32_t cm[3] = {nd.comx, nd.comy, nd.comz};
 #pragma unroll
-            for (int ax3 = 0; ax3 < 3; ++ax3) {
-              int64_t dc = (int32_t)(cn[ax3] - cg[ax3]);
+            for (int a3 = 0; a3 < 3; ++a3) {
+              int64_t dc = (int32_t)(cn[a3] - cg[a3]);
               dc = dc < 0 ? -dc : dc;
               int64_t gap = dc - (lg + ln) / 2;
               if (gap > 0) {
                 touch = false;
                 dist2 += (uint64_t)gap * (uint64_t)gap;
               }
-              int64_t dm = (int32_t)(cm[ax3] - cg[ax3]);
+              int64_t dm = (int32_t)(cm[a3] - cg[a3]);
               dm = (dm < 0 ? -dm : dm) - lg / 2;
               if (dm > 0) dcom2 += (uint64_t)dm * (uint64_t)dm;
             }
-            if (touch || (double)dist2 <= C.rcut_lat2) {
-              bool open = touch || ((double)ln >= C.theta * sqrt((double)dcom2));
+            if (touch || dist2 <= C.skip_d2) {
+              bool open = touch || dcom2 <= C.open_d2[nlevel];
               if (!open)
                 acc = true;
               else if (nd.child < 0)
@@ -198,15 +225,15 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(
           for (int q = 0; q < nch; ++q) sm.stack[w][top + ex + q] = nd.child + q;
           top += tot;
           // particles of opened small leaves
-          int cnt = (leaf && nd.count <= C.B) ? nd.count : 0;
-          int exl = cnt;
+          int lc = (leaf && nd.count <= C.B) ? nd.count : 0;
+          int exl = lc;
           for (int o = 1; o < 32; o <<= 1) {
             int t = __shfl_up_sync(0xffffffffu, exl, o);
             if (lane >= o) exl += t;
           }
           int totl = __shfl_sync(0xffffffffu, exl, 31);
-          exl -= cnt;
-          for (int q = 0; q < cnt; ++q) {
+          exl -= lc;
+          for (int q = 0; q < lc; ++q) {
             int pos = len + exl + q;
             int64_t j = (int64_t)nd.start + q;
             sm.lx[w][pos] = u[j];
@@ -228,8 +255,8 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(
             for (int q0 = 0; q0 < bc; q0 += 32) {
               if (len + 32 > kList) {
                 __syncwarp();
-                eval_list(sm, w, len, active, xi, yi, zi, hi, C, ax, ay, az);
-                npairs += active ? (unsigned long long)len : 0ull;
+                eval_list(sm, w, len, sub, S, active, xi, yi, zi, hi, C, ax, ay, az);
+                npairs += (active && sub == 0) ? (unsigned long long)len : 0ull;
                 len = 0;
                 __syncwarp();
               }
@@ -248,18 +275,24 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(
             }
           }
           if (len > flush_at) {
-            eval_list(sm, w, len, active, xi, yi, zi, hi, C, ax, ay, az);
-            npairs += active ? (unsigned long long)len : 0ull;
+            eval_list(sm, w, len, sub, S, active, xi, yi, zi, hi, C, ax, ay, az);
+            npairs += (active && sub == 0) ? (unsigned long long)len : 0ull;
             len = 0;
             __syncwarp();
           }
         }
         __syncwarp();
-        eval_list(sm, w, len, active, xi, yi, zi, hi, C, ax, ay, az);
-        npairs += active ? (unsigned long long)len : 0ull;
+        eval_list(sm, w, len, sub, S, active, xi, yi, zi, hi, C, ax, ay, az);
+        npairs += (active && sub == 0) ? (unsigned long long)len : 0ull;
         __syncwarp();
+        // combine the S partial sums of each particle (fixed xor tree)
+        for (int o = 1; o < S; o <<= 1) {
+          ax += __shfl_xor_sync(0xffffffffu, ax, o);
+          ay += __shfl_xor_sync(0xffffffffu, ay, o);
+          az += __shfl_xor_sync(0xffffffffu, az, o);
+        }
       }
-      if (active) {
+      if (active && sub == 0) {
         R gx = g[i] + ax, gy = g[cap + i] + ay, gz = g[2 * cap + i] + az;
         g[i] = gx;
         g[cap + i] = gy;
@@ -282,15 +315,16 @@ void walk_impl(dzs_ctx* c, bool tree, bool close_kick, int step) {
   C.scale = (R)c->scale;
   C.rcut2 = (R)(c->rcut * c->rcut);
   C.inv2rs = (R)(1.0 / (2.0 * c->rs));
-  C.c1 = (R)(1.0 / (c->rs * std::sqrt(M_PI)));
+  C.c1 = (R)(2.0 / std::sqrt(M_PI));
   C.gm0 = (R)c->gm0;
   C.h0 = (R)(2.8 * c->eps0);
-  C.rcut_lat2 = c->rcut_lat2;
-  C.theta = c->P.theta;
   C.kick = close_kick ? (R)c->T.kick2[step] : (R)0;
+  C.skip_d2 = c->walk_skip_d2;
+  for (int l = 0; l <= kMaxLevel; ++l) C.open_d2[l] = c->walk_open_d2[l];
   C.B = c->P.leaf_bucket;
   C.close = close_kick ? 1 : 0;
   C.tree = tree ? 1 : 0;
+  C.poly = (c->P.rcut_rs / 2.0 <= (double)kSplitXMax) ? 1 : 0;
   size_t sm = sizeof(WalkSmem<R>);
   static bool attr_done[2] = {false, false};
   if (!attr_done[sizeof(R) == 8]) {
