@@ -110,6 +110,9 @@ struct Buffers {
   int32_t* lvl_count = nullptr;  // [kMaxLevel + 2]
   uint64_t* nsum = nullptr;      // [3][node cap] scratch sums
   int32_t* groups = nullptr;     // [cap]
+  void* wpm = nullptr;           // real [cap]: G m / s^2 per particle (walk, lattice units)
+  void* wph = nullptr;           // real [cap]: spline radius per particle (lattice units)
+  void* wnh = nullptr;           // real [node cap]: node spline radius (lattice units)
   int32_t* group_head = nullptr; // [cap]
   // PM
   void* rho = nullptr;    // real [M^3]

@@ -31,7 +31,7 @@ namespace {
 
 constexpr int kWarps = 4;
 constexpr int kStack = 1024;
-constexpr int kList = 512;
+constexpr int kList = 320;
 
 // Q(t) power-series coefficients, t = 2 x / 2.5 - 1; FP32 rel. error 3.32e-07
 // (generated by gen_split_poly.py)
@@ -40,25 +40,36 @@ __constant__ float kSplitPoly[12] = {1.778296833e+00f, 1.149446721e+00f, 1.66871
                                      2.482135905e-03f, -1.056264300e-03f, 7.980994871e-04f, -3.233674216e-04f};
 constexpr float kSplitXMax = 2.5f;
 
+// interaction-list entry: lattice position and G m / s^2 (lattice units)
 template <class R>
-struct WalkSmem {
-  int32_t stack[kWarps][kStack];
-  uint32_t lx[kWarps][kList], ly[kWarps][kList], lz[kWarps][kList];
-  R lm[kWarps][kList];  // G m of the entry
-  R lh[kWarps][kList];  // spline radius 2.8 eps of the entry
+struct Entry;
+template <>
+struct __align__(16) Entry<float> {
+  uint32_t x, y, z;
+  float m;
+};
+template <>
+struct __align__(8) Entry<double> {
+  uint32_t x, y, z, pad;
+  double m;
 };
 
 template <class R>
+struct WalkSmem {
+  int32_t stack[kWarps][kStack];
+  Entry<R> e[kWarps][kList];
+  R h[kWarps][kList];  // spline radius 2.8 eps of the entry (lattice units)
+};
+
+// everything in lattice units (s = L / 2^32): a = sum (G m / s^2) X fac(R) T(s R)
+template <class R>
 struct WalkConst {
-  R scale;  // L / 2^32
-  R rcut2;  // r_cut^2
-  R inv2rs;  // 1 / (2 r_s)
-  R c1;      // 2 / sqrt(pi)
-  R gm0;     // G m0
-  R h0;      // 2.8 eps0
+  R rcut2;   // (r_cut / s)^2
+  R inv2rs;  // s / (2 r_s)
+  R gm0;     // G m0 / s^2
   R kick;    // closing kick factor
-  uint64_t skip_d2;                   // not skipped iff cube gap^2 <= skip_d2
-  uint64_t open_d2[kMaxLevel + 1];    // opened iff COM distance^2 <= open_d2[level]
+  uint64_t skip_d2;                 // not skipped iff cube gap^2 <= skip_d2
+  uint64_t open_d2[kMaxLevel + 1];  // opened iff COM distance^2 <= open_d2[level]
   int B;
   int close;
   int tree;
@@ -89,30 +100,77 @@ __device__ __forceinline__ double split_factor(double x, int) {
   return erfc(x) + 1.1283791670955126 * x * exp(-x * x);
 }
 
+__device__ __forceinline__ void inv_and_r(float r2, float& r, float& ir) {
+  ir = rsqrtf(r2);
+  r = r2 * ir;
+}
+__device__ __forceinline__ void inv_and_r(double r2, double& r, double& ir) {
+  r = sqrt(r2);
+  ir = 1.0 / r;
+}
+
+template <class R>
+__device__ __forceinline__ void pair(const Entry<R>& E, R he, uint32_t xi, uint32_t yi, uint32_t zi, R hi,
+                                     const WalkConst<R>& C, R& ax, R& ay, R& az) {
+  R dx = (R)(int32_t)(E.x - xi);
+  R dy = (R)(int32_t)(E.y - yi);
+  R dz = (R)(int32_t)(E.z - zi);
+  R r2 = dx * dx + dy * dy + dz * dz;
+  if (r2 > (R)0 && r2 < C.rcut2) {
+    R r, ir;
+    inv_and_r(r2, r, ir);
+    R h = he > hi ? he : hi;
+    R fac = (r >= h) ? ir * ir * ir : spline_fac(r, h);
+    R f = E.m * fac * split_factor(r * C.inv2rs, C.poly);
+    ax += f * dx;
+    ay += f * dy;
+    az += f * dz;
+  }
+}
+
 template <class R>
 __device__ __forceinline__ void eval_list(const WalkSmem<R>& sm, int w, int len, int sub, int S, bool active,
                                           uint32_t xi, uint32_t yi, uint32_t zi, R hi, const WalkConst<R>& C,
                                           R& ax, R& ay, R& az) {
   if (!active) return;
-  for (int e = sub; e < len; e += S) {
-    R dx = (R)(int32_t)(sm.lx[w][e] - xi) * C.scale;
-    R dy = (R)(int32_t)(sm.ly[w][e] - yi) * C.scale;
-    R dz = (R)(int32_t)(sm.lz[w][e] - zi) * C.scale;
-    R r2 = dx * dx + dy * dy + dz * dz;
-    if (r2 > (R)0 && r2 < C.rcut2) {
-      R r = sqrt(r2);
-      R h = sm.lh[w][e] > hi ? sm.lh[w][e] : hi;
-      R fac;
-      if (r >= h) {
-        R ir = (R)1 / r;
-        fac = ir * ir * ir;
-      } else {
-        fac = spline_fac(r, h);
-      }
-      R f = sm.lm[w][e] * fac * split_factor(r * C.inv2rs, C.poly);
-      ax += f * dx;
-      ay += f * dy;
-      az += f * dz;
+  int e = sub;
+  for (; e + S < len; e += 2 * S) {
+    Entry<R> E0 = sm.e[w][e], E1 = sm.e[w][e + S];
+    R h0 = sm.h[w][e], h1 = sm.h[w][e + S];
+    pair(E0, h0, xi, yi, zi, hi, C, ax, ay, az);
+    pair(E1, h1, xi, yi, zi, hi, C, ax, ay, az);
+  }
+  if (e < len) pair(sm.e[w][e], sm.h[w][e], xi, yi, zi, hi, C, ax, ay, az);
+}
+
+template <class R>
+__device__ __forceinline__ int warp_incl_scan(int v, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
+  }
+  return v;
+}
+
+// per-step walk inputs: particle G m / s^2 and spline radius, node spline radius
+template <class R>
+__global__ void k_walk_prep(const int32_t* __restrict__ d_n, const uint32_t* __restrict__ k,
+                            const int32_t* __restrict__ lvl, const Node* __restrict__ nodes, R* __restrict__ pm,
+                            R* __restrict__ ph, R* __restrict__ nh, R gm0, R h0) {
+  const int64_t n = *d_n;
+  int64_t nn = 0;
+  for (int j = 0; j <= kMaxLevel; ++j) nn += lvl[j];
+  const int64_t m = n > nn ? n : nn;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    if (i < n) {
+      uint32_t kk = k[i];
+      pm[i] = gm0 * (R)kk;
+      ph[i] = kk == 1 ? h0 : h0 * cbrt((R)kk);
+    }
+    if (i < nn) {
+      uint32_t km = nodes[i].kmax;
+      nh[i] = km == 1 ? h0 : h0 * cbrt((R)km);
     }
   }
 }
@@ -120,9 +178,9 @@ __device__ __forceinline__ void eval_list(const WalkSmem<R>& sm, int w, int len,
 template <class R>
 __global__ void __launch_bounds__(kWarps * 32) k_walk(
     const int32_t* __restrict__ groups, const uint64_t* __restrict__ counters, unsigned int* __restrict__ next,
-    const Node* __restrict__ nodes, int64_t cap, const uint32_t* __restrict__ u, const uint32_t* __restrict__ k,
-    R* __restrict__ p, R* __restrict__ g, WalkConst<R> C, uint32_t* __restrict__ err,
-    unsigned long long* __restrict__ pairs) {
+    const Node* __restrict__ nodes, const R* __restrict__ nh, int64_t cap, const uint32_t* __restrict__ u,
+    const R* __restrict__ pm, const R* __restrict__ ph, R* __restrict__ p, R* __restrict__ g, WalkConst<R> C,
+    uint32_t* __restrict__ err, unsigned long long* __restrict__ pairs) {
   extern __shared__ unsigned char smem_raw[];
   WalkSmem<R>& sm = *reinterpret_cast<WalkSmem<R>*>(smem_raw);
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -151,7 +209,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(
         xi = u[i];
         yi = u[cap + i];
         zi = u[2 * cap + i];
-        hi = C.h0 * cbrt((R)k[i]);
+        hi = ph[i];
       }
       R ax = 0, ay = 0, az = 0;
       if (C.tree) {
@@ -201,20 +259,18 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(
           unsigned am = __ballot_sync(0xffffffffu, acc);
           if (acc) {
             int pos = len + __popc(am & lt);
-            sm.lx[w][pos] = nd.comx;
-            sm.ly[w][pos] = nd.comy;
-            sm.lz[w][pos] = nd.comz;
-            sm.lm[w][pos] = C.gm0 * (R)nd.mass;
-            sm.lh[w][pos] = C.h0 * cbrt((R)nd.kmax);
+            Entry<R> E;
+            E.x = nd.comx;
+            E.y = nd.comy;
+            E.z = nd.comz;
+            E.m = C.gm0 * (R)nd.mass;
+            sm.e[w][pos] = E;
+            sm.h[w][pos] = nh[ni];
           }
           len += __popc(am);
           // children of opened inner nodes onto the stack
           int nch = inner ? (int)((nd.meta >> 8) & 0xff) : 0;
-          int ex = nch;
-          for (int o = 1; o < 32; o <<= 1) {
-            int t = __shfl_up_sync(0xffffffffu, ex, o);
-            if (lane >= o) ex += t;
-          }
+          int ex = warp_incl_scan<R>(nch, lane);
           int tot = __shfl_sync(0xffffffffu, ex, 31);
           ex -= nch;
           if (top + tot > kStack) {
@@ -224,24 +280,33 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(
           }
           for (int q = 0; q < nch; ++q) sm.stack[w][top + ex + q] = nd.child + q;
           top += tot;
-          // particles of opened small leaves
+          // particles of opened small leaves, copied cooperatively: item t of
+          // the round belongs to the lane whose inclusive end first exceeds t
           int lc = (leaf && nd.count <= C.B) ? nd.count : 0;
-          int exl = lc;
-          for (int o = 1; o < 32; o <<= 1) {
-            int t = __shfl_up_sync(0xffffffffu, exl, o);
-            if (lane >= o) exl += t;
-          }
-          int totl = __shfl_sync(0xffffffffu, exl, 31);
-          exl -= lc;
-          for (int q = 0; q < lc; ++q) {
-            int pos = len + exl + q;
-            int64_t j = (int64_t)nd.start + q;
-            sm.lx[w][pos] = u[j];
-            sm.ly[w][pos] = u[cap + j];
-            sm.lz[w][pos] = u[2 * cap + j];
-            uint32_t kj = k[j];
-            sm.lm[w][pos] = C.gm0 * (R)kj;
-            sm.lh[w][pos] = C.h0 * cbrt((R)kj);
+          int incl = warp_incl_scan<R>(lc, lane);
+          int totl = __shfl_sync(0xffffffffu, incl, 31);
+          int lstart = leaf ? nd.start : 0;
+          for (int b0 = 0; b0 < totl; b0 += 32) {
+            int t = b0 + lane;
+            int src = 0;
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1) {
+              int v = __shfl_sync(0xffffffffu, incl, src + step - 1);
+              if (v <= t) src += step;
+            }
+            int send = __shfl_sync(0xffffffffu, incl, src);
+            int scnt = __shfl_sync(0xffffffffu, lc, src);
+            int sst = __shfl_sync(0xffffffffu, lstart, src);
+            if (t < totl) {
+              int64_t j = (int64_t)sst + (t - (send - scnt));
+              Entry<R> E;
+              E.x = u[j];
+              E.y = u[cap + j];
+              E.z = u[2 * cap + j];
+              E.m = pm[j];
+              sm.e[w][len + t] = E;
+              sm.h[w][len + t] = ph[j];
+            }
           }
           len += totl;
           __syncwarp();
@@ -260,17 +325,18 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(
                 len = 0;
                 __syncwarp();
               }
-              int m = bc - q0 < 32 ? bc - q0 : 32;
-              if (lane < m) {
+              int mm = bc - q0 < 32 ? bc - q0 : 32;
+              if (lane < mm) {
                 int64_t j = (int64_t)bs + q0 + lane;
-                sm.lx[w][len + lane] = u[j];
-                sm.ly[w][len + lane] = u[cap + j];
-                sm.lz[w][len + lane] = u[2 * cap + j];
-                uint32_t kj = k[j];
-                sm.lm[w][len + lane] = C.gm0 * (R)kj;
-                sm.lh[w][len + lane] = C.h0 * cbrt((R)kj);
+                Entry<R> E;
+                E.x = u[j];
+                E.y = u[cap + j];
+                E.z = u[2 * cap + j];
+                E.m = pm[j];
+                sm.e[w][len + lane] = E;
+                sm.h[w][len + lane] = ph[j];
               }
-              len += m;
+              len += mm;
               __syncwarp();
             }
           }
@@ -311,13 +377,11 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(
 
 template <class R>
 void walk_impl(dzs_ctx* c, bool tree, bool close_kick, int step) {
+  const double s = c->scale;
   WalkConst<R> C;
-  C.scale = (R)c->scale;
-  C.rcut2 = (R)(c->rcut * c->rcut);
-  C.inv2rs = (R)(1.0 / (2.0 * c->rs));
-  C.c1 = (R)(2.0 / std::sqrt(M_PI));
-  C.gm0 = (R)c->gm0;
-  C.h0 = (R)(2.8 * c->eps0);
+  C.rcut2 = (R)((c->rcut / s) * (c->rcut / s));
+  C.inv2rs = (R)(s / (2.0 * c->rs));
+  C.gm0 = (R)(c->gm0 / (s * s));
   C.kick = close_kick ? (R)c->T.kick2[step] : (R)0;
   C.skip_d2 = c->walk_skip_d2;
   for (int l = 0; l <= kMaxLevel; ++l) C.open_d2[l] = c->walk_open_d2[l];
@@ -325,6 +389,11 @@ void walk_impl(dzs_ctx* c, bool tree, bool close_kick, int step) {
   C.close = close_kick ? 1 : 0;
   C.tree = tree ? 1 : 0;
   C.poly = (c->P.rcut_rs / 2.0 <= (double)kSplitXMax) ? 1 : 0;
+  R* pm = (R*)c->B.wpm;
+  R* ph = (R*)c->B.wph;
+  R* nh = (R*)c->B.wnh;
+  k_walk_prep<R><<<grid_for(c->node_cap), kThreads, 0, c->stream>>>(c->B.n, c->B.k, c->B.lvl_count, c->B.nodes, pm,
+                                                                     ph, nh, C.gm0, (R)(2.8 * c->eps0 / s));
   size_t sm = sizeof(WalkSmem<R>);
   static bool attr_done[2] = {false, false};
   if (!attr_done[sizeof(R) == 8]) {
@@ -338,15 +407,15 @@ void walk_impl(dzs_ctx* c, bool tree, bool close_kick, int step) {
   int grid = (per_sm > 0 ? per_sm : 1) * (nsm > 0 ? nsm : 1);
   unsigned int* next = (unsigned int*)(c->B.counters + 6);
   cudaMemsetAsync(next, 0, sizeof(unsigned int), c->stream);
-  k_walk<R><<<grid, kWarps * 32, sm, c->stream>>>(c->B.groups, c->B.counters, next, c->B.nodes, c->cap, c->B.u,
-                                                  c->B.k, (R*)c->B.p, (R*)c->B.g, C, c->B.err,
+  k_walk<R><<<grid, kWarps * 32, sm, c->stream>>>(c->B.groups, c->B.counters, next, c->B.nodes, nh, c->cap, c->B.u,
+                                                  pm, ph, (R*)c->B.p, (R*)c->B.g, C, c->B.err,
                                                   (unsigned long long*)(c->B.counters + 4));
 }
 
 }  // namespace
 
 void launch_walk(dzs_ctx* c, bool tree, bool close_kick, int step) {
-  c->launches += 1;
+  c->launches += 2;
   if (c->fp64)
     walk_impl<double>(c, tree, close_kick, step);
   else
