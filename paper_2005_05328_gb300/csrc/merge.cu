@@ -56,17 +56,39 @@ __global__ void k_prefix_totals(const int32_t* __restrict__ d_n, int64_t cap, co
   }
 }
 
+// block c scans row c (channel c) of the chunk totals, 1024 at a time
 __global__ void k_prefix_scan_totals(uint64_t* __restrict__ tot, int nchunks) {
-  // one thread per channel: chunks are few (n / 1024)
-  if (threadIdx.x >= 4) return;
-  uint64_t* row = tot + (int64_t)threadIdx.x * (nchunks + 1);
-  uint64_t s = 0;
-  for (int b = 0; b < nchunks; ++b) {
-    uint64_t v = row[b];
-    row[b] = s;
-    s += v;
+  __shared__ unsigned long long woff[32];
+  __shared__ unsigned long long carry, block_total;
+  uint64_t* row = tot + (int64_t)blockIdx.x * (nchunks + 1);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < nchunks; base += blockDim.x) {
+    int i = base + threadIdx.x;
+    unsigned long long v = i < nchunks ? row[i] : 0ull, inc = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned long long t = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += t;
+    }
+    if (lane == 31) woff[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+      unsigned long long t = lane < nw ? woff[lane] : 0ull, ti = t;
+      for (int o = 1; o < 32; o <<= 1) {
+        unsigned long long q = __shfl_up_sync(0xffffffffu, ti, o);
+        if (lane >= o) ti += q;
+      }
+      if (lane < nw) woff[lane] = ti - t;
+      if (lane == nw - 1) block_total = ti;
+    }
+    __syncthreads();
+    if (i < nchunks) row[i] = carry + woff[w] + inc - v;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += block_total;
+    __syncthreads();
   }
-  row[nchunks] = s;
+  if (threadIdx.x == 0) row[nchunks] = carry;
 }
 
 __global__ void k_prefix_apply(const int32_t* __restrict__ d_n, int64_t cap, const uint32_t* __restrict__ u,
@@ -237,7 +259,7 @@ void launch_merge(dzs_ctx* c, uint64_t rlat) {
   int nchunks = (int)((c->cap + kChunk) / kChunk);
   uint64_t* tot = (uint64_t*)B.blocksum;
   k_prefix_totals<<<nchunks, 256, 0, c->stream>>>(B.n, c->cap, B.u, B.k, tot);
-  k_prefix_scan_totals<<<1, 32, 0, c->stream>>>(tot, nchunks);
+  k_prefix_scan_totals<<<4, 1024, 0, c->stream>>>(tot, nchunks);
   k_prefix_apply<<<nchunks, 256, 0, c->stream>>>(B.n, c->cap, B.u, B.k, tot, nchunks, B.prefix);
   int32_t* keep = B.iscan + (c->cap + 1);
   int32_t* rank = B.iscan;
