@@ -195,6 +195,7 @@ void launch_ics(dzs_ctx* c);
 void launch_to_double(dzs_ctx* c, const void* src, int64_t count, double* dst);
 void launch_from_double(dzs_ctx* c, const double* src, int64_t count, void* dst);
 void launch_fft_init(dzs_ctx* c);
+void upload_fft_constants(int dev);  // register-FFT twiddles, once per device
 template <class R>
 void fft_r2c_3d(dzs_ctx* c, const R* in, cplx<R>* out, int n, const cplx<R>* tw);
 template <class R>

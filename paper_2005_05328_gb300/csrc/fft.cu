@@ -9,9 +9,13 @@
 //   X      -- same along ix; for the Poisson solve the forward FFT, the Green
 //             multiply and the inverse FFT are fused in one pass;
 //   Y inverse, Z c2r.
-// In-block transform: radix-2 decimation in time on shared memory, columns
-// interleaved (element e of column q at e * W + q), bit-reversed load.
-// Twiddles come from an FP64 host table (cast to the working precision).
+// Each length-n transform is a four-step FFT, n = N1 N2 (N1 >= N2, powers of
+// two): N2 register FFTs of length N1 (input stride N2), twiddle W_n^(j2 k1),
+// one exchange through shared memory, N1 register FFTs of length N2.  A thread
+// owns one length-N1 and one length-N2 sub-transform of one column, so a
+// column costs two register FFTs and one shared-memory round trip instead of
+// log2(n) barrier-separated radix-2 stages.  Twiddles come from FP64 host
+// tables (W_32 table in constant memory, W_n in global memory).
 #include <cmath>
 #include <vector>
 
@@ -20,183 +24,314 @@
 namespace dzs {
 namespace {
 
-constexpr int kFftThreads = 256;
-constexpr int kSmemBytes = 64 * 1024;
+__constant__ cplx<float> kTw32f[32];   // exp(-2 pi i t / 32)
+__constant__ cplx<double> kTw32d[32];
 
-template <class R>
-__device__ void fft_smem(cplx<R>* buf, int n, int logn, int W, const cplx<R>* __restrict__ tw, bool inverse) {
-  const int nb = (n >> 1) * W;
-  for (int s = 0; s < logn; ++s) {
-    const int half = 1 << s;
-    const int stride = n >> (s + 1);  // twiddle index stride
-    for (int q = threadIdx.x; q < nb; q += blockDim.x) {
-      int col = q % W, b = q / W;
-      int j = b & (half - 1);
-      int i0 = ((b >> s) << (s + 1)) + j;
-      int i1 = i0 + half;
-      cplx<R> w = tw[j * stride];
-      if (inverse) w.y = -w.y;
-      cplx<R> a = buf[i0 * W + col];
-      cplx<R> bb = cmul(buf[i1 * W + col], w);
-      buf[i0 * W + col] = {a.x + bb.x, a.y + bb.y};
-      buf[i1 * W + col] = {a.x - bb.x, a.y - bb.y};
+__device__ __forceinline__ cplx<float> tw32(int t, float) { return kTw32f[t]; }
+__device__ __forceinline__ cplx<double> tw32(int t, double) { return kTw32d[t]; }
+
+constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n >> 1); }
+constexpr int brevc(int v, int bits) {
+  int r = 0;
+  for (int i = 0; i < bits; ++i) r |= ((v >> i) & 1) << (bits - 1 - i);
+  return r;
+}
+
+// in-register radix-2 DIT FFT of length K (natural order in and out);
+// inv selects the conjugate twiddles
+template <class R, int K>
+__device__ __forceinline__ void reg_fft(cplx<R> (&a)[K], bool inv) {
+  constexpr int L = ilog2c(K);
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    const int j = brevc(i, L);
+    if (j > i) {
+      cplx<R> t = a[i];
+      a[i] = a[j];
+      a[j] = t;
     }
-    __syncthreads();
+  }
+#pragma unroll
+  for (int s = 0; s < L; ++s) {
+    const int half = 1 << s;
+#pragma unroll
+    for (int b = 0; b < K / 2; ++b) {
+      const int j = b & (half - 1);
+      const int i0 = ((b >> s) << (s + 1)) + j, i1 = i0 + half;
+      cplx<R> w = tw32(j * (32 / (2 * half)), R(0));
+      if (inv) w.y = -w.y;
+      cplx<R> x = a[i0], y = cmul(a[i1], w);
+      a[i0] = {x.x + y.x, x.y + y.y};
+      a[i1] = {x.x - y.x, x.y - y.y};
+    }
   }
 }
 
-__device__ __forceinline__ int bitrev(int e, int logn) { return (int)(__brev((unsigned)e) >> (32 - logn)); }
-
-// Z pass, real -> half spectrum.  Block handles W row pairs.
+// W_n^t from the half table tw[t] = exp(-2 pi i t / n), t < n / 2
 template <class R>
-__global__ void k_fft_z_r2c(const R* __restrict__ in, cplx<R>* __restrict__ out, int n, int logn, int W,
-                            int64_t npairs, const cplx<R>* __restrict__ tw) {
+__device__ __forceinline__ cplx<R> twn(const cplx<R>* __restrict__ tw, int t, int n, bool inv) {
+  t &= n - 1;
+  cplx<R> w = t < n / 2 ? tw[t] : cplx<R>{-tw[t - n / 2].x, -tw[t - n / 2].y};
+  if (inv) w.y = -w.y;
+  return w;
+}
+
+template <int N>
+struct Split {
+  static constexpr int N1 = 1 << ((ilog2c(N) + 1) / 2);
+  static constexpr int N2 = N / N1;
+};
+
+// ---- generic four-step pieces on one column held in shared memory
+// step A: thread (col, j2) transforms x[j1 N2 + j2] over j1, twiddles, and
+// writes Y[k1 N2 + j2] back into the same column
+template <class R, int N>
+__device__ __forceinline__ void stepA_smem(cplx<R>* buf, int W, int col, int j2, const cplx<R>* __restrict__ tw,
+                                           bool inv) {
+  constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
+  cplx<R> a[N1];
+#pragma unroll
+  for (int j1 = 0; j1 < N1; ++j1) a[j1] = buf[(j1 * N2 + j2) * W + col];
+  reg_fft<R, N1>(a, inv);
+#pragma unroll
+  for (int k1 = 0; k1 < N1; ++k1) a[k1] = cmul(a[k1], twn(tw, j2 * k1, N, inv));
+#pragma unroll
+  for (int k1 = 0; k1 < N1; ++k1) buf[(k1 * N2 + j2) * W + col] = a[k1];
+}
+
+// step B: thread (col, k1) transforms Y[k1 N2 + j2] over j2; result element
+// k1 + N1 k2 is b[k2]
+template <class R, int N>
+__device__ __forceinline__ void stepB_smem(const cplx<R>* buf, int W, int col, int k1, cplx<R> (&b)[Split<N>::N2],
+                                           bool inv) {
+  constexpr int N2 = Split<N>::N2;
+#pragma unroll
+  for (int j2 = 0; j2 < N2; ++j2) b[j2] = buf[(k1 * N2 + j2) * W + col];
+  reg_fft<R, N2>(b, inv);
+}
+
+// ---- Z pass, real -> half spectrum.  Block: W row pairs, W * N1 threads.
+template <class R, int N>
+__global__ void k_fft_z_r2c(const R* __restrict__ in, cplx<R>* __restrict__ out, int W, int64_t npairs,
+                            const cplx<R>* __restrict__ tw) {
+  constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2, HN = N / 2 + 1;
   extern __shared__ unsigned char smem_raw[];
   cplx<R>* buf = reinterpret_cast<cplx<R>*>(smem_raw);
   const int64_t p0 = (int64_t)blockIdx.x * W;
-  const int hn = n / 2 + 1;
-  for (int q = threadIdx.x; q < n * W; q += blockDim.x) {
-    int col = q / n, e = q % n;
+  // coalesced load: element e of pair col at buf[e * W + col]
+  for (int q = threadIdx.x; q < N * W; q += blockDim.x) {
+    int col = q / N, e = q % N;
     int64_t pr = p0 + col;
     cplx<R> v = {0, 0};
-    if (pr < npairs) v = {in[(2 * pr) * n + e], in[(2 * pr + 1) * n + e]};
-    buf[bitrev(e, logn) * W + col] = v;
+    if (pr < npairs) v = {in[(2 * pr) * N + e], in[(2 * pr + 1) * N + e]};
+    buf[e * W + col] = v;
   }
   __syncthreads();
-  fft_smem(buf, n, logn, W, tw, false);
-  for (int q = threadIdx.x; q < hn * W; q += blockDim.x) {
-    int col = q / hn, k = q % hn;
-    int64_t pr = p0 + col;
+  const int col = threadIdx.x % W, r = threadIdx.x / W;
+  if (r < N2) stepA_smem<R, N>(buf, W, col, r, tw, false);
+  __syncthreads();
+  cplx<R> b[N2];
+  if (r < N1) stepB_smem<R, N>(buf, W, col, r, b, false);
+  __syncthreads();
+  if (r < N1) {
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) buf[(r + N1 * k2) * W + col] = b[k2];
+  }
+  __syncthreads();
+  // unpack: X_a = (Z_k + conj Z_-k) / 2,  X_b = (Z_k - conj Z_-k) / (2 i)
+  for (int q = threadIdx.x; q < HN * W; q += blockDim.x) {
+    int c = q / HN, k = q % HN;
+    int64_t pr = p0 + c;
     if (pr >= npairs) continue;
-    cplx<R> z = buf[(k % n) * W + col], zc = buf[((n - k) % n) * W + col];
-    // X_a = (Z_k + conj Z_-k) / 2,  X_b = (Z_k - conj Z_-k) / (2 i)
-    cplx<R> xa = {(R)0.5 * (z.x + zc.x), (R)0.5 * (z.y - zc.y)};
-    cplx<R> xb = {(R)0.5 * (z.y + zc.y), (R)-0.5 * (z.x - zc.x)};
-    out[(2 * pr) * hn + k] = xa;
-    out[(2 * pr + 1) * hn + k] = xb;
+    cplx<R> z = buf[(k % N) * W + c], zc = buf[((N - k) % N) * W + c];
+    out[(2 * pr) * HN + k] = {(R)0.5 * (z.x + zc.x), (R)0.5 * (z.y - zc.y)};
+    out[(2 * pr + 1) * HN + k] = {(R)0.5 * (z.y + zc.y), (R)-0.5 * (z.x - zc.x)};
   }
 }
 
-// Z pass inverse, half spectrum -> real (unnormalised).  Block: W row pairs.
-template <class R>
-__global__ void k_fft_z_c2r(const cplx<R>* __restrict__ in, R* __restrict__ out, int n, int logn, int W,
-                            int64_t npairs, const cplx<R>* __restrict__ tw) {
+// ---- Z pass inverse, half spectrum -> real (unnormalised).
+template <class R, int N>
+__global__ void k_fft_z_c2r(const cplx<R>* __restrict__ in, R* __restrict__ out, int W, int64_t npairs,
+                            const cplx<R>* __restrict__ tw) {
+  constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2, HN = N / 2 + 1;
   extern __shared__ unsigned char smem_raw[];
   cplx<R>* buf = reinterpret_cast<cplx<R>*>(smem_raw);
   const int64_t p0 = (int64_t)blockIdx.x * W;
-  const int hn = n / 2 + 1;
-  for (int q = threadIdx.x; q < n * W; q += blockDim.x) {
-    int col = q / n, k = q % n;
+  for (int q = threadIdx.x; q < N * W; q += blockDim.x) {
+    int col = q / N, k = q % N;
     int64_t pr = p0 + col;
     cplx<R> z = {0, 0};
     if (pr < npairs) {
       cplx<R> a, b;
-      if (k < hn) {
-        a = in[(2 * pr) * hn + k];
-        b = in[(2 * pr + 1) * hn + k];
+      if (k < HN) {
+        a = in[(2 * pr) * HN + k];
+        b = in[(2 * pr + 1) * HN + k];
       } else {
-        a = in[(2 * pr) * hn + (n - k)];
-        b = in[(2 * pr + 1) * hn + (n - k)];
+        a = in[(2 * pr) * HN + (N - k)];
+        b = in[(2 * pr + 1) * HN + (N - k)];
         a.y = -a.y;
         b.y = -b.y;
       }
       z = {a.x - b.y, a.y + b.x};  // a + i b
     }
-    buf[bitrev(k, logn) * W + col] = z;
+    buf[k * W + col] = z;
   }
   __syncthreads();
-  fft_smem(buf, n, logn, W, tw, true);
-  for (int q = threadIdx.x; q < n * W; q += blockDim.x) {
-    int col = q / n, e = q % n;
-    int64_t pr = p0 + col;
+  const int col = threadIdx.x % W, r = threadIdx.x / W;
+  if (r < N2) stepA_smem<R, N>(buf, W, col, r, tw, true);
+  __syncthreads();
+  cplx<R> b[N2];
+  if (r < N1) stepB_smem<R, N>(buf, W, col, r, b, true);
+  __syncthreads();
+  if (r < N1) {
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) buf[(r + N1 * k2) * W + col] = b[k2];
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < N * W; q += blockDim.x) {
+    int c = q / N, e = q % N;
+    int64_t pr = p0 + c;
     if (pr >= npairs) continue;
-    cplx<R> z = buf[e * W + col];
-    out[(2 * pr) * n + e] = z.x;
-    out[(2 * pr + 1) * n + e] = z.y;
+    cplx<R> z = buf[e * W + c];
+    out[(2 * pr) * N + e] = z.x;
+    out[(2 * pr + 1) * N + e] = z.y;
   }
 }
 
-// Column pass along Y (axis = 1) or X (axis = 0) of the half spectrum.
+// ---- column pass along Y (axis 1) or X (axis 0) of the half spectrum.
 // mode 0 forward, 1 inverse, 2 forward + Green multiply + inverse (X only).
-template <class R>
-__global__ void k_fft_cols(cplx<R>* __restrict__ spec, int n, int logn, int W, int axis, int mode,
-                           const cplx<R>* __restrict__ tw, const R* __restrict__ gtab, R gfac) {
+// Block: one line (ix for Y, iy for X) and W consecutive kz columns.
+template <class R, int N>
+__global__ void k_fft_cols(cplx<R>* __restrict__ spec, int W, int axis, int mode, const cplx<R>* __restrict__ tw,
+                           const R* __restrict__ gtab, R gfac) {
+  constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2, HN = N / 2 + 1;
   extern __shared__ unsigned char smem_raw[];
   cplx<R>* buf = reinterpret_cast<cplx<R>*>(smem_raw);
-  const int hn = n / 2 + 1;
-  const int ncb = (hn + W - 1) / W;            // column blocks per line
-  const int line = blockIdx.x / ncb;           // fixed other index (ix for Y, iy for X)
+  const int ncb = (HN + W - 1) / W;
+  const int line = blockIdx.x / ncb;
   const int kz0 = (blockIdx.x % ncb) * W;
-  const int64_t es = axis == 1 ? (int64_t)hn : (int64_t)n * hn;     // element stride
-  const int64_t base = axis == 1 ? (int64_t)line * n * hn : (int64_t)line * hn;
-  for (int q = threadIdx.x; q < n * W; q += blockDim.x) {
-    int e = q / W, col = q % W;
-    cplx<R> v = {0, 0};
-    if (kz0 + col < hn) v = spec[base + e * es + kz0 + col];
-    buf[bitrev(e, logn) * W + col] = v;
+  const int64_t es = axis == 1 ? (int64_t)HN : (int64_t)N * HN;
+  const int64_t base = axis == 1 ? (int64_t)line * N * HN : (int64_t)line * HN;
+  const int col = threadIdx.x % W, r = threadIdx.x / W;
+  const bool valid = kz0 + col < HN;
+  const bool inv = mode == 1;
+  // step A straight from global memory (coalesced across columns)
+  if (r < N2) {
+    cplx<R> a[N1];
+#pragma unroll
+    for (int j1 = 0; j1 < N1; ++j1) a[j1] = valid ? spec[base + (j1 * N2 + r) * es + kz0 + col] : cplx<R>{0, 0};
+    reg_fft<R, N1>(a, inv);
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) buf[(k1 * N2 + r) * W + col] = cmul(a[k1], twn(tw, r * k1, N, inv));
   }
   __syncthreads();
-  fft_smem(buf, n, logn, W, tw, mode == 1);
-  if (mode == 2) {
-    // Green function: gtab holds per-axis k^2 (first n) and W_CIC^2 (next n)
-    const R* k2t = gtab;
-    const R* wt = gtab + n;
-    for (int q = threadIdx.x; q < n * W; q += blockDim.x) {
-      int e = q / W, col = q % W;  // e = kx index
-      int kz = kz0 + col;
+  cplx<R> b[N2];
+  if (r < N1) stepB_smem<R, N>(buf, W, col, r, b, inv);
+  if (mode != 2) {
+    if (r < N1 && valid) {
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) spec[base + (r + N1 * k2) * es + kz0 + col] = b[k2];
+    }
+    return;
+  }
+  // Green multiply on element kx = r + N1 k2 (gtab: per-axis k^2, W_CIC, r_s^2)
+  const R* k2t = gtab;
+  const R* wt = gtab + N;
+  const int kz = kz0 + col;
+  if (r < N1) {
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) {
+      const int kx = r + N1 * k2;
       R gv = 0;
-      if (kz < hn) {
-        R k2 = k2t[e] + k2t[line] + k2t[kz];
-        if (k2 > (R)0) {
-          R w = wt[e] * wt[line] * wt[kz];
-          gv = gfac * exp(-k2 * gtab[2 * n]) / (k2 * w * w);
+      if (valid) {
+        R kk = k2t[kx] + k2t[line] + k2t[kz];
+        if (kk > (R)0) {
+          R wv = wt[kx] * wt[line] * wt[kz];
+          gv = gfac * exp(-kk * gtab[2 * N]) / (kk * wv * wv);
         }
       }
-      cplx<R> v = buf[e * W + col];
-      buf[e * W + col] = {v.x * gv, v.y * gv};
+      b[k2] = {b[k2].x * gv, b[k2].y * gv};
     }
-    __syncthreads();
-    // bit-reverse in place for the inverse transform
-    for (int q = threadIdx.x; q < n * W; q += blockDim.x) {
-      int e = q / W, col = q % W;
-      int r = bitrev(e, logn);
-      if (r > e) {
-        cplx<R> t = buf[e * W + col];
-        buf[e * W + col] = buf[r * W + col];
-        buf[r * W + col] = t;
-      }
-    }
-    __syncthreads();
-    fft_smem(buf, n, logn, W, tw, true);
   }
-  for (int q = threadIdx.x; q < n * W; q += blockDim.x) {
-    int e = q / W, col = q % W;
-    if (kz0 + col < hn) spec[base + e * es + kz0 + col] = buf[e * W + col];
+  // inverse with the roles of N1 and N2 swapped: this thread holds the
+  // elements r + N1 k2, i.e. one length-N2 sub-sequence of stride N1
+  __syncthreads();
+  if (r < N1) {
+    reg_fft<R, N2>(b, true);
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) buf[(k2 * N1 + r) * W + col] = cmul(b[k2], twn(tw, r * k2, N, true));
+  }
+  __syncthreads();
+  if (r < N2) {
+    cplx<R> a[N1];
+#pragma unroll
+    for (int j = 0; j < N1; ++j) a[j] = buf[(r * N1 + j) * W + col];
+    reg_fft<R, N1>(a, true);
+    if (valid) {
+#pragma unroll
+      for (int k1 = 0; k1 < N1; ++k1) spec[base + (r + N2 * k1) * es + kz0 + col] = a[k1];
+    }
   }
 }
 
-template <class R>
-int cols_per_block(int n) {
-  int w = kSmemBytes / (n * (int)sizeof(cplx<R>));
-  if (w > 64) w = 64;
-  if (w < 1) w = 1;
+template <class R, int N>
+int cols_per_block() {
+  // W * N1 threads per block, at most 256; shared memory W * N * sizeof(cplx)
+  int w = 256 / Split<N>::N1;
+  while (w > 1 && (size_t)w * N * sizeof(cplx<R>) > 48 * 1024) w >>= 1;
   return w;
 }
 
-int ilog2(int n) {
-  int l = 0;
-  while ((1 << l) < n) ++l;
-  return l;
+template <class R, int N>
+void launch_r2c_zy(dzs_ctx* c, const R* in, cplx<R>* out, const cplx<R>* tw, bool do_x) {
+  const int W = cols_per_block<R, N>();
+  const int threads = W * Split<N>::N1;
+  const size_t sm = (size_t)N * W * sizeof(cplx<R>);
+  const int64_t npairs = (int64_t)N * N / 2;
+  k_fft_z_r2c<R, N><<<(unsigned)((npairs + W - 1) / W), threads, sm, c->stream>>>(in, out, W, npairs, tw);
+  const int ncb = (N / 2 + 1 + W - 1) / W;
+  k_fft_cols<R, N><<<N * ncb, threads, sm, c->stream>>>(out, W, 1, 0, tw, nullptr, (R)0);
+  if (do_x) k_fft_cols<R, N><<<N * ncb, threads, sm, c->stream>>>(out, W, 0, 0, tw, nullptr, (R)0);
+}
+
+template <class R, int N>
+void launch_c2r(dzs_ctx* c, cplx<R>* in, R* out, const cplx<R>* tw, const R* green, R gfac) {
+  const int W = cols_per_block<R, N>();
+  const int threads = W * Split<N>::N1;
+  const size_t sm = (size_t)N * W * sizeof(cplx<R>);
+  const int64_t npairs = (int64_t)N * N / 2;
+  const int ncb = (N / 2 + 1 + W - 1) / W;
+  k_fft_cols<R, N><<<N * ncb, threads, sm, c->stream>>>(in, W, 0, green ? 2 : 1, tw, green, gfac);
+  k_fft_cols<R, N><<<N * ncb, threads, sm, c->stream>>>(in, W, 1, 1, tw, nullptr, (R)0);
+  k_fft_z_c2r<R, N><<<(unsigned)((npairs + W - 1) / W), threads, sm, c->stream>>>(in, out, W, npairs, tw);
 }
 
 template <class R>
-void set_smem_attrs() {
-  static bool done = false;
-  if (done) return;
-  cudaFuncSetAttribute(k_fft_z_r2c<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
-  cudaFuncSetAttribute(k_fft_z_c2r<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
-  cudaFuncSetAttribute(k_fft_cols<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
-  done = true;
+void dispatch_r2c(dzs_ctx* c, const R* in, cplx<R>* out, int n, const cplx<R>* tw, bool do_x) {
+  switch (n) {
+    case 8: launch_r2c_zy<R, 8>(c, in, out, tw, do_x); break;
+    case 16: launch_r2c_zy<R, 16>(c, in, out, tw, do_x); break;
+    case 32: launch_r2c_zy<R, 32>(c, in, out, tw, do_x); break;
+    case 64: launch_r2c_zy<R, 64>(c, in, out, tw, do_x); break;
+    case 128: launch_r2c_zy<R, 128>(c, in, out, tw, do_x); break;
+    case 256: launch_r2c_zy<R, 256>(c, in, out, tw, do_x); break;
+    case 512: launch_r2c_zy<R, 512>(c, in, out, tw, do_x); break;
+    default: break;  // sizes are validated at context creation
+  }
+}
+
+template <class R>
+void dispatch_c2r(dzs_ctx* c, cplx<R>* in, R* out, int n, const cplx<R>* tw, const R* green, R gfac) {
+  switch (n) {
+    case 8: launch_c2r<R, 8>(c, in, out, tw, green, gfac); break;
+    case 16: launch_c2r<R, 16>(c, in, out, tw, green, gfac); break;
+    case 32: launch_c2r<R, 32>(c, in, out, tw, green, gfac); break;
+    case 64: launch_c2r<R, 64>(c, in, out, tw, green, gfac); break;
+    case 128: launch_c2r<R, 128>(c, in, out, tw, green, gfac); break;
+    case 256: launch_c2r<R, 256>(c, in, out, tw, green, gfac); break;
+    case 512: launch_c2r<R, 512>(c, in, out, tw, green, gfac); break;
+    default: break;
+  }
 }
 
 }  // namespace
@@ -204,41 +339,21 @@ void set_smem_attrs() {
 // forward 3D r2c of an n^3 real array
 template <class R>
 void fft_r2c_3d(dzs_ctx* c, const R* in, cplx<R>* out, int n, const cplx<R>* tw) {
-  set_smem_attrs<R>();
-  int logn = ilog2(n), W = cols_per_block<R>(n);
-  int64_t npairs = (int64_t)n * n / 2;
-  size_t sm = (size_t)n * W * sizeof(cplx<R>);
-  k_fft_z_r2c<R><<<(unsigned)((npairs + W - 1) / W), kFftThreads, sm, c->stream>>>(in, out, n, logn, W, npairs, tw);
-  int ncb = (n / 2 + 1 + W - 1) / W;
-  k_fft_cols<R><<<n * ncb, kFftThreads, sm, c->stream>>>(out, n, logn, W, 1, 0, tw, nullptr, (R)0);
-  k_fft_cols<R><<<n * ncb, kFftThreads, sm, c->stream>>>(out, n, logn, W, 0, 0, tw, nullptr, (R)0);
+  dispatch_r2c<R>(c, in, out, n, tw, true);
 }
 
-// inverse 3D c2r; when green != nullptr the X pass first runs forward and
-// multiplies by the Green function (the spectrum then holds the Y/Z-forward
-// data of the density and the X forward is fused here)
+// inverse 3D c2r; when green != nullptr the X pass runs forward, multiplies by
+// the Green function and runs inverse (the spectrum then holds the Z/Y-forward
+// data of the density)
 template <class R>
 void fft_c2r_3d(dzs_ctx* c, cplx<R>* in, R* out, int n, const cplx<R>* tw, const R* green, R gfac) {
-  set_smem_attrs<R>();
-  int logn = ilog2(n), W = cols_per_block<R>(n);
-  int64_t npairs = (int64_t)n * n / 2;
-  size_t sm = (size_t)n * W * sizeof(cplx<R>);
-  int ncb = (n / 2 + 1 + W - 1) / W;
-  k_fft_cols<R><<<n * ncb, kFftThreads, sm, c->stream>>>(in, n, logn, W, 0, green ? 2 : 1, tw, green, gfac);
-  k_fft_cols<R><<<n * ncb, kFftThreads, sm, c->stream>>>(in, n, logn, W, 1, 1, tw, nullptr, (R)0);
-  k_fft_z_c2r<R><<<(unsigned)((npairs + W - 1) / W), kFftThreads, sm, c->stream>>>(in, out, n, logn, W, npairs, tw);
+  dispatch_c2r<R>(c, in, out, n, tw, green, gfac);
 }
 
 // forward Z and Y passes only (the X forward is fused with the Green multiply)
 template <class R>
 void fft_r2c_zy(dzs_ctx* c, const R* in, cplx<R>* out, int n, const cplx<R>* tw) {
-  set_smem_attrs<R>();
-  int logn = ilog2(n), W = cols_per_block<R>(n);
-  int64_t npairs = (int64_t)n * n / 2;
-  size_t sm = (size_t)n * W * sizeof(cplx<R>);
-  k_fft_z_r2c<R><<<(unsigned)((npairs + W - 1) / W), kFftThreads, sm, c->stream>>>(in, out, n, logn, W, npairs, tw);
-  int ncb = (n / 2 + 1 + W - 1) / W;
-  k_fft_cols<R><<<n * ncb, kFftThreads, sm, c->stream>>>(out, n, logn, W, 1, 0, tw, nullptr, (R)0);
+  dispatch_r2c<R>(c, in, out, n, tw, false);
 }
 
 template void fft_r2c_3d<float>(dzs_ctx*, const float*, cplx<float>*, int, const cplx<float>*);
@@ -260,5 +375,21 @@ std::vector<cplx<R>> twiddles(int n) {
 }
 template std::vector<cplx<float>> twiddles<float>(int);
 template std::vector<cplx<double>> twiddles<double>(int);
+
+// the length-32 register-FFT table in constant memory (both precisions)
+void upload_fft_constants(int dev) {
+  static bool done[256] = {false};
+  if (dev < 0 || dev >= 256 || done[dev]) return;
+  cplx<float> tf[32];
+  cplx<double> td[32];
+  for (int t = 0; t < 32; ++t) {
+    double ang = -2.0 * M_PI * (double)t / 32.0;
+    td[t] = {std::cos(ang), std::sin(ang)};
+    tf[t] = {(float)td[t].x, (float)td[t].y};
+  }
+  cudaMemcpyToSymbol(kTw32f, tf, sizeof tf);
+  cudaMemcpyToSymbol(kTw32d, td, sizeof td);
+  done[dev] = true;
+}
 
 }  // namespace dzs

@@ -153,6 +153,7 @@ std::vector<cplx<R>> twiddles(int n);
 
 // twiddles of size M and the per-axis Green tables (k^2, W_CIC, r_s^2)
 void launch_fft_init(dzs_ctx* c) {
+  upload_fft_constants(c->dev);
   const int M = c->M;
   std::vector<double> k2(M), w(M);
   double kf = 2.0 * M_PI / c->P.box;
