@@ -194,8 +194,9 @@ DZS_API dzs_status dzs_get_mesh(dzs_ctx* c, int32_t which, double* out);
  * [2] pair evaluations (interaction-list entries x group particles) summed
  * since the last dzs_ics / dzs_set_state / dzs_set_profiling, [3] device error
  * word, [4] kernels launched by this context so far, [5] lightcone records
- * written so far. */
-DZS_API dzs_status dzs_get_counters(dzs_ctx* c, uint64_t out[6]);
+  * written so far, [6] deepest tree-walk stack use (entries, of 1024),
+ * [7] tree-walk node tests and [8] traversal rounds summed like [2]. */
+DZS_API dzs_status dzs_get_counters(dzs_ctx* c, uint64_t out[9]);
 
 /* profile categories of dzs_get_profile */
 enum {

@@ -228,7 +228,7 @@ def dzs_get_profile(h):
 
 
 def dzs_get_counters(h):
-    out = np.zeros(6, np.uint64)
+    out = np.zeros(9, np.uint64)
     _check(load().dzs_get_counters(h, _ptr(out)), h)
     return out
 

@@ -572,7 +572,8 @@ dzs_status dzs_set_state(dzs_ctx* c, const uint32_t* u, const double* p, const d
   int32_t nn = (int32_t)n;
   CK(cudaMemcpy(c->B.n, &nn, sizeof nn, cudaMemcpyHostToDevice));
   CK(cudaMemset(c->B.err, 0, 16));
-  CK(cudaMemset(c->B.counters + 4, 0, sizeof(uint64_t)));
+  CK(cudaMemset(c->B.counters + 4, 0, 4 * sizeof(uint64_t)));  // pairs and stack depth (4, 7)
+  CK(cudaMemset(c->B.counters + 12, 0, 2 * sizeof(uint64_t)));  // node tests, rounds
   c->step = step;
   c->have_state = true;
   if (g) {
@@ -679,7 +680,8 @@ dzs_status dzs_set_profiling(dzs_ctx* c, int32_t enable) {
     c->prof_ms[i] = 0;
     c->prof_calls[i] = 0;
   }
-  CK(cudaMemsetAsync(c->B.counters + 4, 0, sizeof(uint64_t), c->stream));
+  CK(cudaMemsetAsync(c->B.counters + 4, 0, 4 * sizeof(uint64_t), c->stream));
+  CK(cudaMemsetAsync(c->B.counters + 12, 0, 2 * sizeof(uint64_t), c->stream));
   c->prof_on = enable != 0;
   return DZS_OK;
 }
@@ -704,7 +706,7 @@ dzs_status dzs_get_profile(dzs_ctx* c, double ms[DZS_PROF_N], uint64_t calls[DZS
   return DZS_OK;
 }
 
-dzs_status dzs_get_counters(dzs_ctx* c, uint64_t out[6]) {
+dzs_status dzs_get_counters(dzs_ctx* c, uint64_t out[9]) {
   dzs_status s = guard(c);
   if (s) return s;
   if (!out) return fail(c, DZS_EINVAL, "out is NULL");
@@ -719,6 +721,9 @@ dzs_status dzs_get_counters(dzs_ctx* c, uint64_t out[6]) {
   out[3] = err;
   out[4] = c->launches;
   out[5] = ctr[0];
+  out[6] = ctr[7];
+  out[7] = ctr[12];
+  out[8] = ctr[13];
   return DZS_OK;
 }
 

@@ -16,9 +16,9 @@
 // threshold once per context: the walk compares integers only and builds the
 // same interaction set as the CPU reference, with no FP64 in the walk.
 // The list lives in shared memory; when it fills, all 32 lanes evaluate it:
-// a group of c particles gets 32 / next_pow2(c) lanes per particle, each lane
-// summing every S-th entry, combined by a fixed xor-shuffle tree (the result
-// is deterministic).  Pair force: softened 1/r^3 times
+// a group of c particles gets S = floor(32 / c) lanes per particle, each lane
+// summing every S-th entry, combined by a fixed shuffle tree (the result is
+// deterministic).  Pair force: softened 1/r^3 times
 // T(r) = erfc(x) + (2/sqrt(pi)) x exp(-x^2), x = r / 2 r_s, zero at r = 0 and
 // r >= r_cut.  FP32 evaluates T = exp(-x^2) Q(x) with a fitted polynomial
 // (gen_split_poly.py, relative error 3.3e-7); FP64 calls erfc and exp.
@@ -70,11 +70,17 @@ struct WalkConst {
   R kick;    // closing kick factor
   uint64_t skip_d2;                 // not skipped iff cube gap^2 <= skip_d2
   uint64_t open_d2[kMaxLevel + 1];  // opened iff COM distance^2 <= open_d2[level]
+  float skip_lo, skip_hi;           // FP32 bounds of skip_d2 (relative margin 2^-20)
+  float open_lo[kMaxLevel + 1], open_hi[kMaxLevel + 1];
   int B;
   int close;
   int tree;
   int poly;  // FP32: use the fitted split polynomial (x_max <= 2.5)
 };
+
+__device__ __forceinline__ uint64_t exact_d2(const uint32_t (&v)[3]) {
+  return (uint64_t)v[0] * v[0] + (uint64_t)v[1] * v[1] + (uint64_t)v[2] * v[2];
+}
 
 template <class R>
 __device__ __forceinline__ R spline_fac(R r, R h) {
@@ -115,8 +121,9 @@ __device__ __forceinline__ void pair(const Entry<R>& E, R he, uint32_t xi, uint3
   R dx = (R)(int32_t)(E.x - xi);
   R dy = (R)(int32_t)(E.y - yi);
   R dz = (R)(int32_t)(E.z - zi);
-  R r2 = dx * dx + dy * dy + dz * dz;
-  if (r2 > (R)0 && r2 < C.rcut2) {
+  // the self pair has dx = 0: the tiny bias keeps its term finite and exactly 0
+  R r2 = dx * dx + dy * dy + dz * dz + (R)1e-20;
+  if (r2 < C.rcut2) {
     R r, ir;
     inv_and_r(r2, r, ir);
     R h = he > hi ? he : hi;
@@ -187,6 +194,8 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(
   const unsigned lt = (1u << lane) - 1u;
   const int64_t ngroups = (int64_t)counters[2];
   unsigned long long npairs = 0;
+  int maxtop = 0;  // deepest stack use of this warp (diagnostic)
+  unsigned long long ntests = 0, nrounds = 0;  // node tests and traversal rounds (diagnostic)
   const int flush_at = kList - 32 * (C.B > 1 ? C.B : 1) - 32;
   for (;;) {
     int64_t gi = 0;
@@ -195,12 +204,12 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(
     if (gi >= ngroups) break;
     const Node gn = nodes[groups[gi]];
     const int glevel = gn.meta & 0xff;
-    const int64_t lg = 1ll << (32 - glevel);
+    const uint32_t hg = 1u << (31 - glevel);  // half side of the group cube
     for (int c0 = 0; c0 < gn.count; c0 += 32) {
-      // lanes per particle S = 32 / next_pow2(particles in this chunk)
       const int cnt = gn.count - c0 < 32 ? gn.count - c0 : 32;
-      const int S = 32 >> (32 - __clz(cnt - 1 > 0 ? cnt - 1 : 0));
-      const int mine = lane / S, sub = lane % S;
+      // S = floor(32 / c) lanes per particle (c * S <= 32 lanes busy)
+      const int S = 32 / cnt;
+      const int mine = lane / S, sub = lane - mine * S;
       const int64_t i = (int64_t)gn.start + c0 + mine;
       const bool active = mine < cnt;
       uint32_t xi = 0, yi = 0, zi = 0;
@@ -219,6 +228,8 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(
         __syncwarp();
         while (top > 0) {
           const int npop = top < 32 ? top : 32;
+          ntests += npop;
+          nrounds += 1;
           int ni = lane < npop ? sm.stack[w][top - npop + lane] : -1;
           top -= npop;
           __syncwarp();
@@ -227,26 +238,46 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(
           if (ni >= 0) {
             nd = nodes[ni];
             const int nlevel = (int)(nd.meta & 0xff);
-            const int64_t ln = 1ll << (32 - nlevel);
+            // 32-bit gaps (half extents: group hg <= 2^31, node hn <= 2^30 below
+            // the root, so hg + hn < 2^32); squared sums in FP32 decide unless
+            // they fall within 2^-20 of the exact integer threshold, where the
+            // uint64 sum decides -- the same decision as the integer rule
             bool touch = true;
-            uint64_t dist2 = 0, dcom2 = 0;
+            uint32_t gp[3], dmv[3];
+            float d2f = 0.f, c2f = 0.f;
             const uint32_t cn[3] = {nd.cx, nd.cy, nd.cz}, cg[3] = {gn.cx, gn.cy, gn.cz};
             const uint32_t cm[3] = {nd.comx, nd.comy, nd.comz};
+            const uint32_t hn = nlevel == 0 ? 0u : (1u << (31 - nlevel));
 #pragma unroll
             for (int a3 = 0; a3 < 3; ++a3) {
-              int64_t dc = (int32_t)(cn[a3] - cg[a3]);
-              dc = dc < 0 ? -dc : dc;
-              int64_t gap = dc - (lg + ln) / 2;
-              if (gap > 0) {
-                touch = false;
-                dist2 += (uint64_t)gap * (uint64_t)gap;
-              }
-              int64_t dm = (int32_t)(cm[a3] - cg[a3]);
-              dm = (dm < 0 ? -dm : dm) - lg / 2;
-              if (dm > 0) dcom2 += (uint64_t)dm * (uint64_t)dm;
+              int32_t ds = (int32_t)(cn[a3] - cg[a3]);
+              uint32_t dc = ds < 0 ? 0u - (uint32_t)ds : (uint32_t)ds;
+              uint32_t h = hg + hn;
+              uint32_t gap = (nlevel > 0 && dc > h) ? dc - h : 0u;
+              touch = touch && gap == 0u;
+              gp[a3] = gap;
+              d2f = fmaf((float)gap, (float)gap, d2f);
+              int32_t ms = (int32_t)(cm[a3] - cg[a3]);
+              uint32_t mc = ms < 0 ? 0u - (uint32_t)ms : (uint32_t)ms;
+              uint32_t dm = mc > hg ? mc - hg : 0u;
+              dmv[a3] = dm;
+              c2f = fmaf((float)dm, (float)dm, c2f);
             }
-            if (touch || dist2 <= C.skip_d2) {
-              bool open = touch || dcom2 <= C.open_d2[nlevel];
+            bool keep = touch;
+            if (!touch) {
+              if (d2f <= C.skip_lo)
+                keep = true;
+              else if (d2f < C.skip_hi)
+                keep = exact_d2(gp) <= C.skip_d2;
+            }
+            if (keep) {
+              bool open = touch;
+              if (!open) {
+                if (c2f <= C.open_lo[nlevel])
+                  open = true;
+                else if (c2f < C.open_hi[nlevel])
+                  open = exact_d2(dmv) <= C.open_d2[nlevel];
+              }
               if (!open)
                 acc = true;
               else if (nd.child < 0)
@@ -280,6 +311,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(
           }
           for (int q = 0; q < nch; ++q) sm.stack[w][top + ex + q] = nd.child + q;
           top += tot;
+          maxtop = top > maxtop ? top : maxtop;
           // particles of opened small leaves, copied cooperatively: item t of
           // the round belongs to the lane whose inclusive end first exceeds t
           int lc = (leaf && nd.count <= C.B) ? nd.count : 0;
@@ -351,11 +383,17 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(
         eval_list(sm, w, len, sub, S, active, xi, yi, zi, hi, C, ax, ay, az);
         npairs += (active && sub == 0) ? (unsigned long long)len : 0ull;
         __syncwarp();
-        // combine the S partial sums of each particle (fixed xor tree)
+        // combine the S partial sums of each particle: fixed shuffle tree
+        // within each run of S lanes (deterministic for a given group size)
         for (int o = 1; o < S; o <<= 1) {
-          ax += __shfl_xor_sync(0xffffffffu, ax, o);
-          ay += __shfl_xor_sync(0xffffffffu, ay, o);
-          az += __shfl_xor_sync(0xffffffffu, az, o);
+          const bool in = sub + o < S;
+          R tx = __shfl_down_sync(0xffffffffu, ax, o), ty = __shfl_down_sync(0xffffffffu, ay, o);
+          R tz = __shfl_down_sync(0xffffffffu, az, o);
+          if (in) {
+            ax += tx;
+            ay += ty;
+            az += tz;
+          }
         }
       }
       if (active && sub == 0) {
@@ -373,6 +411,9 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(
   }
   for (int o = 16; o > 0; o >>= 1) npairs += __shfl_down_sync(0xffffffffu, npairs, o);
   if (lane == 0 && npairs) atomicAdd(pairs, npairs);
+  if (lane == 0) atomicMax(pairs + 3, (unsigned long long)maxtop);
+  if (lane == 0) atomicAdd(pairs + 8, ntests);
+  if (lane == 0) atomicAdd(pairs + 9, nrounds);
 }
 
 template <class R>
@@ -385,6 +426,16 @@ void walk_impl(dzs_ctx* c, bool tree, bool close_kick, int step) {
   C.kick = close_kick ? (R)c->T.kick2[step] : (R)0;
   C.skip_d2 = c->walk_skip_d2;
   for (int l = 0; l <= kMaxLevel; ++l) C.open_d2[l] = c->walk_open_d2[l];
+  // FP32 bounds around each integer threshold: a float sum below lo is surely
+  // <= T, one at or above hi surely > T (FP32 sum error < 2^-21 relative)
+  auto lo_of = [](uint64_t t) { return std::nextafter((float)((double)t * (1.0 - 0x1p-20)), 0.0f); };
+  auto hi_of = [](uint64_t t) { return std::nextafter((float)((double)t * (1.0 + 0x1p-20)), INFINITY); };
+  C.skip_lo = lo_of(C.skip_d2);
+  C.skip_hi = hi_of(C.skip_d2);
+  for (int l = 0; l <= kMaxLevel; ++l) {
+    C.open_lo[l] = lo_of(C.open_d2[l]);
+    C.open_hi[l] = hi_of(C.open_d2[l]);
+  }
   C.B = c->P.leaf_bucket;
   C.close = close_kick ? 1 : 0;
   C.tree = tree ? 1 : 0;
