@@ -32,8 +32,47 @@ METRIC = "particle-steps/s DZS FP32 vs plain FP64 at stated force error; mocks/h
 UNIT = "particle-steps/s"
 # nominal FP32 pipe: 152 SMs x 128 lanes x 2 flop (FMA) x 2.07 GHz max SM clock
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-# arithmetic of one pair evaluation of the FP32 walk ("walk roofline")
-FLOP_PER_PAIR = 38
+# FP32 arithmetic of one pair evaluation of the walk (FMA = 2; rsqrt, exp2 = 1):
+# r^2 6, rsqrt 1, r 1, r^-3 2, x 1, t 2, split polynomial 22, exp 4, force 2,
+# accumulate 6 ("walk roofline")
+FLOP_PER_PAIR = 47
+
+# algorithmic HBM bytes per step of the streaming stages, FP32 state
+# (u 12 B, p 12 B, g 12 B, k 4 B, id 4 B, flags 1 B per particle; mesh M^3);
+# derivation in DESIGN.md ("per-stage bytes")
+STAGE_BYTES = {
+    "kick_drift": lambda n, m3: 90 * n,
+    "sort": lambda n, m3: 326 * n,
+    "merge": lambda n, m3: 194 * n,
+    "tree": lambda n, m3: 95 * n,
+    "pm": lambda n, m3: 56.3 * m3 + 40 * n,
+}
+
+
+def active_counts(dzs, P, stream, warmup, steps):
+    """Particle count before each timed step, from an untimed replay of the
+    same deterministic run (the timed loop itself never synchronises)."""
+    import torch
+    ctx = dzs.Context(P, stream=stream.cuda_stream)
+    counts = []
+    with torch.cuda.stream(stream):
+        ctx.ics()
+        step = 0
+        for _ in range(warmup):
+            ctx.step(1)
+            step += 1
+        for _ in range(steps):
+            if step == P.nsteps:
+                ctx.ics()
+                step = 0
+                for _ in range(warmup):
+                    ctx.step(1)
+                    step += 1
+            counts.append(ctx.count()[0])
+            ctx.step(1)
+            step += 1
+    ctx.close()
+    return counts
 
 C2 = dict(n1d=128, mesh=256, box=256.0, merge_level=3, seed=2, sigma8=0.8)
 
@@ -174,6 +213,7 @@ def main():
     import torch
     import paper_2005_05328_gb300 as dzs
     from paper_2005_05328_gb300 import build as libbuild
+    from paper_2005_05328_gb300 import replicas as R
 
     if world > 1:
         import torch.distributed as dist
@@ -187,6 +227,7 @@ def main():
     stream = torch.cuda.Stream()
     P = workload_params(dzs, dzs.FP32)
     P.device = local
+    P.seed = R.replica_seed(C2["seed"], rank)  # each replica runs its own mock
     ctx = dzs.Context(P, stream=stream.cuda_stream)
     n0 = P.n1d ** 3
     nst = P.nsteps
@@ -243,13 +284,9 @@ def main():
         pairs = int(cnt[2])
         n_final, _ = ctx.count()
     t_local = ms / 1e3
-    if world > 1:
-        t = torch.tensor([t_local], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    else:
-        t_max = t_local
-    value = n0 * args.steps * world / t_max
+    units_total, t_max = R.aggregate(n0 * args.steps, t_local,
+                                     device=torch.device("cuda", local) if world > 1 else None)
+    value = R.throughput(units_total, t_max)
 
     # e2e through the public API with host buffers (rank 0 measures, others replicate)
     e2e = None
@@ -258,8 +295,20 @@ def main():
 
     if rank != 0:
         return
-    # roofline of the dominant stage
+    # HBM rooflines of the streaming stages (algorithmic bytes / stage time)
+    counts = active_counts(dzs, P, stream, args.warmup, args.steps)
+    m3 = P.mesh ** 3
     pk = peaks()
+    hbm = float(pk.get("hbm_gbs", 6800.0))  # measured copy bandwidth, else the 6.8 TB/s fallback
+    stage_roof = {}
+    for name, fn in STAGE_BYTES.items():
+        ms_s = prof[name][0]
+        if ms_s <= 0:
+            continue
+        gb = sum(fn(n, m3) for n in counts) / 1e9
+        stage_roof[name] = {"bound": "hbm", "algorithmic_GB": gb, "achieved_GBs": gb / (ms_s / 1e3),
+                            "frac": gb / (ms_s / 1e3) / hbm}
+    # roofline of the dominant stage
     dom = max(prof, key=lambda k: prof[k][0])
     walk_ms, walk_calls = prof["walk"]
     walk_avg_s = walk_ms / 1e3 / max(1, walk_calls)
@@ -282,6 +331,7 @@ def main():
                    "n_active_end": int(n_final)},
         "roofline": roof,
         "stage_ms": {k: v[0] for k, v in prof.items()},
+        "stage_roofline": stage_roof,
         "gpu_launches": launches,
         "clocks": clocks,
         "e2e": e2e,
