@@ -194,6 +194,33 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def time_variant(dzs, P, stream, warmup, steps, budget_s=120.0):
+    """Device time of `steps` KDK steps after `warmup` steps from the ICs, on a
+    fresh context (CUDA events on the context stream).  Stops early once the
+    timed steps exceed budget_s seconds; returns (steps timed, seconds)."""
+    import torch
+    ctx = dzs.Context(P, stream=stream.cuda_stream)
+    done, total = 0, 0.0
+    with torch.cuda.stream(stream):
+        ctx.ics()
+        ctx.step(warmup)
+        torch.cuda.synchronize()
+        while done < steps and ctx.count()[1] < P.nsteps:
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            chunk = min(8, steps - done)
+            a.record(stream)
+            got = ctx.step(chunk)
+            b.record(stream)
+            b.synchronize()
+            total += a.elapsed_time(b) / 1e3
+            done += got
+            if got == 0 or total > budget_s:
+                break
+    ctx.close()
+    return done, total
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -202,6 +229,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-compare", action="store_true", help="skip the plain-FP64 and no-DZS runs")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -336,6 +364,20 @@ def main():
         "clocks": clocks,
         "e2e": e2e,
     }
+    if world == 1 and not args.no_compare:
+        # the metric compares DZS FP32 with the plain FP64 path (no DZS, FP64
+        # forces) and, for the DZS speed-up itself, FP32 without DZS
+        comp = {}
+        for name, kw in (("plain_fp64_no_dzs", dict(precision=dzs.FP64, dzs_on=0)),
+                         ("fp32_no_dzs", dict(precision=dzs.FP32, dzs_on=0))):
+            Pv = workload_params(dzs, kw["precision"])
+            Pv.dzs_on = kw["dzs_on"]
+            Pv.device = local
+            k, sec = time_variant(dzs, Pv, stream, args.warmup, args.steps)
+            comp[name] = {"value": n0 * k / sec if sec > 0 else None, "unit": UNIT, "steps_timed": k,
+                          "ms_per_step": 1e3 * sec / max(1, k),
+                          "ratio_dzs_fp32_over_this": (value / (n0 * k / sec)) if sec > 0 else None}
+        line["comparisons"] = comp
     if world == 1 and not args.no_cpu_baseline:
         try:
             line["cpu_baseline"] = cpu_baseline()
