@@ -30,7 +30,7 @@ class Params(C.Structure):
         ("dzs_on", C.c_int32), ("merge_level", C.c_int32), ("rlc_mode", C.c_int32),
         ("rs_cells", C.c_double), ("rcut_rs", C.c_double), ("theta", C.c_double),
         ("soft_frac", C.c_double), ("theta_dzs", C.c_double), ("buffer_cells", C.c_double),
-        ("seed", C.c_uint64),
+        ("seed", C.c_uint64), ("criterion", C.c_int32), ("pad_", C.c_int32), ("alpha_dyn", C.c_double),
     ]
 
 
@@ -50,7 +50,7 @@ DEFAULTS = dict(n1d=32, mesh=64, box=64.0, omega_m=0.3, omega_l=0.7, hubble=0.7,
                 sigma8=0.8, ns=0.96, z_init=49.0, nsteps=96, leaf_bucket=8,
                 walk_group=32, dzs_on=1, merge_level=2, rlc_mode=0, rs_cells=1.25,
                 rcut_rs=4.5, theta=0.5, soft_frac=1.0 / 40.0, theta_dzs=0.1,
-                buffer_cells=2.0, seed=1)
+                buffer_cells=2.0, seed=1, criterion=0, alpha_dyn=0.01)
 
 
 def lib():
@@ -91,7 +91,8 @@ def _declare(L):
         "dzso_pair_factor": (d, [P, d, d]),
         "dzso_count_groups": (i64, [P, i64, vp, vp, vp]),
         "dzso_interaction_count": (i64, [P, i64, vp, vp, i64]),
-        "dzso_merge": (i64, [P, i64, u64, vp, vp, vp, vp, vp]),
+        "dzso_merge": (i64, [P, i64, u64, d, vp, vp, vp, vp, vp]),
+        "dzso_amin2": (d, [i64, vp, vp]),
         "dzso_merge_jmin": (i32, [P]),
         "dzso_merge_threshold": (u64, [P, u64, i32]),
         "dzso_accel": (None, [P, i64, vp, vp, vp, i32, vp, i64]),
@@ -256,13 +257,22 @@ def merge_jmin(P): return lib().dzso_merge_jmin(C.byref(P))
 def merge_threshold(P, rlat, level): return lib().dzso_merge_threshold(C.byref(P), int(rlat), level)
 
 
-def merge(P, rlat, state):
-    """DZS merge on a Morton-sorted state dict; returns a new state dict."""
+def amin2(g, fl):
+    g = _c(g, np.float64); fl = _c(fl, np.uint8)
+    return lib().dzso_amin2(g.shape[1], _ptr(g), _ptr(fl))
+
+
+def merge(P, rlat, state, amin2_value=None):
+    """DZS merge on a Morton-sorted state dict; returns a new state dict.  The
+    dynamical criterion uses amin2_value, else the state's g and flags."""
     n = state["u"].shape[1]
+    if amin2_value is None:
+        amin2_value = amin2(state["g"], state["fl"]) if "g" in state else float("inf")
     u = _c(state["u"], np.uint32).copy(); p = _c(state["p"], np.float64).copy()
     k = _c(state["k"], np.uint32).copy(); i = _c(state["id"], np.uint32).copy()
     fl = _c(state["fl"], np.uint8).copy()
-    m = lib().dzso_merge(C.byref(P), n, int(rlat), _ptr(u), _ptr(p), _ptr(k), _ptr(i), _ptr(fl))
+    m = lib().dzso_merge(C.byref(P), n, int(rlat), float(amin2_value), _ptr(u), _ptr(p), _ptr(k), _ptr(i),
+                         _ptr(fl))
     return dict(u=u.reshape(-1)[:3 * m].reshape(3, m).copy(), p=p.reshape(-1)[:3 * m].reshape(3, m).copy(),
                 k=k[:m].copy(), id=i[:m].copy(), fl=fl[:m].copy())
 

@@ -14,6 +14,10 @@
  *     single particle is left alone; l_max = 2^(merge_level-1) lambda;
  *   - integer test: merge iff d_COM^2 > T^2, T = R_lat + b_lat + ceil(l_lat /
  *     theta_dzs) (lattice units; T >= 2^32 never merges);
+ *   - dynamical criterion (Sec. 2.2.1: Eq. 2 with d -> D_n of Eq. 3 and
+ *     |a_old| -> the smallest |a| of the particles inside the lightcone, i.e.
+ *     not yet crossed): merge iff D > 0 and G M_n l^2 / D^4 < alpha a_min,
+ *     D = (sqrt(d_COM^2) - R_lat - b_lat) L / 2^32, in FP64 in this order;
  *   - new particle: k = sum k, u = floor((2 S + K) / (2 K)), p = (sum k p) / K
  *     with the FP64 sum taken left to right in Morton order, id = min id,
  *     flags = merged | crossed.  The survivors keep their Morton order.
@@ -45,6 +49,7 @@ typedef struct {
   const dzso_params* P;
   int64_t n;
   uint64_t rlat;
+  double amin2;
   int32_t jmin;
   const uint64_t* key;
   const uint32_t* u;
@@ -72,10 +77,31 @@ static void keep_one(mctx* c, int64_t i) {
   c->ofl[o] = c->fl[i];
 }
 
+static int qualifies_dynamical(mctx* c, int level, uint64_t K, const uint32_t com[3]) {
+  const dzso_params* P = c->P;
+  double lat = 4294967296.0;
+  uint64_t blat = (uint64_t)floor(P->buffer_cells * lat / P->mesh);
+  uint64_t d2 = 0;
+  for (int ax = 0; ax < 3; ++ax) {
+    int64_t off = (int64_t)(int32_t)(com[ax] - 2147483648u);
+    d2 += (uint64_t)(off * off);
+  }
+  double scale = P->box / lat;
+  double D = (sqrt((double)d2) - (double)(c->rlat + blat)) * scale;
+  if (!(D > 0.0)) return 0;
+  double n0 = (double)P->n1d * P->n1d * P->n1d;
+  double gm0 = 1.5 * P->omega_m * P->box * P->box * P->box / (4.0 * M_PI * n0);
+  double l = ldexp(P->box, -level);
+  double D2 = D * D;
+  double lhs = gm0 * (double)K * (l * l) / (D2 * D2);
+  double rhs = P->alpha_dyn * sqrt(c->amin2);
+  return lhs < rhs;
+}
+
 static int qualifies(mctx* c, int level, int64_t s, int64_t e, uint64_t K, const uint32_t com[3]) {
   (void)s;
   (void)e;
-  (void)K;
+  if (c->P->criterion == 1) return qualifies_dynamical(c, level, K, com);
   uint64_t t = dzso_merge_threshold(c->P, c->rlat, level);
   if (t >= 4294967296ull) return 0;
   uint64_t d2 = 0;
@@ -133,7 +159,18 @@ static void merge_cell(mctx* c, int level, int64_t s, int64_t e) {
   }
 }
 
-int64_t dzso_merge(const dzso_params* P, int64_t n, uint64_t rlat, uint32_t* u,
+double dzso_amin2(int64_t n, const double* g, const uint8_t* fl) {
+  double m = INFINITY;
+  for (int64_t i = 0; i < n; ++i) {
+    if (fl[i] & DZSO_FL_CROSSED) continue;
+    double gx = g[i], gy = g[(size_t)n + i], gz = g[2 * (size_t)n + i];
+    double a2 = gx * gx + gy * gy + gz * gz;
+    if (a2 < m) m = a2;
+  }
+  return m;
+}
+
+int64_t dzso_merge(const dzso_params* P, int64_t n, uint64_t rlat, double amin2, uint32_t* u,
                    double* p, uint32_t* k, uint32_t* id, uint8_t* fl) {
   if (n == 0) return 0;
   uint64_t* key = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)n);
@@ -143,6 +180,7 @@ int64_t dzso_merge(const dzso_params* P, int64_t n, uint64_t rlat, uint32_t* u,
   c.P = P;
   c.n = n;
   c.rlat = rlat;
+  c.amin2 = amin2;
   c.jmin = dzso_merge_jmin(P);
   c.key = key;
   c.u = u;

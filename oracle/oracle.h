@@ -61,6 +61,9 @@ typedef struct {
   double theta_dzs;     /* DZS geometric merge angle (Sec. 2.2.1) */
   double buffer_cells;  /* buffer b in mesh cells (Eq. 3) */
   uint64_t seed;
+  int32_t criterion;    /* 0: geometric l/D < theta_dzs; 1: dynamical (Eq. 2 with D of Eq. 3) */
+  int32_t pad_;
+  double alpha_dyn;     /* dynamical merge parameter alpha */
 } dzso_params;
 
 typedef struct {
@@ -121,9 +124,13 @@ int64_t dzso_interaction_count(const dzso_params* P, int64_t n, const uint32_t* 
                                const uint32_t* k, int64_t group_index);
 
 /* ---- DZS merge (merge.c) ----
- * In place on Morton-sorted arrays; returns the new particle count. */
-int64_t dzso_merge(const dzso_params* P, int64_t n, uint64_t rlat, uint32_t* u,
+ * In place on Morton-sorted arrays; returns the new particle count.  amin2 is
+ * the squared smallest acceleration inside the lightcone (dynamical
+ * criterion only; see dzso_amin2). */
+int64_t dzso_merge(const dzso_params* P, int64_t n, uint64_t rlat, double amin2, uint32_t* u,
                    double* p, uint32_t* k, uint32_t* id, uint8_t* fl);
+/* min over particles not yet crossed of |g|^2 (g [3][n]); +inf if none */
+double dzso_amin2(int64_t n, const double* g, const uint8_t* fl);
 int32_t dzso_merge_jmin(const dzso_params* P);
 uint64_t dzso_merge_threshold(const dzso_params* P, uint64_t rlat, int32_t level);
 

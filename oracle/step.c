@@ -171,6 +171,9 @@ int64_t dzso_step(const dzso_params* P, int32_t step, int64_t n, uint32_t* u,
   step_tab t = step_tables(P, step);
   int64_t nr = dzso_kick_drift_cross(P, step, n, u, p, g, k, id, fl, rec);
   if (nrec) *nrec = nr;
+  /* a_old for the dynamical merge criterion: the previous accelerations of the
+   * particles still inside the lightcone (g and fl share the pre-sort order) */
+  double amin2 = dzso_amin2(n, g, fl);
   /* Morton sort, stable */
   uint64_t* key = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(n > 0 ? n : 1));
   int64_t* perm = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
@@ -202,7 +205,7 @@ int64_t dzso_step(const dzso_params* P, int32_t step, int64_t n, uint32_t* u,
   free(tfl);
   free(key);
   free(perm);
-  if (P->dzs_on) n = dzso_merge(P, n, t.rlat1, u, p, k, id, fl);
+  if (P->dzs_on) n = dzso_merge(P, n, t.rlat1, amin2, u, p, k, id, fl);
   dzso_accel(P, n, u, k, g, 3, NULL, 0);
   for (size_t j = 0; j < 3 * (size_t)n; ++j) p[j] = p[j] + g[j] * t.kick2;
   return n;
