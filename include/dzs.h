@@ -60,6 +60,7 @@ typedef enum {
 
 enum { DZS_RLC_SWEEP = 0, DZS_RLC_PHYSICAL = 1 };
 enum { DZS_FP32 = 0, DZS_FP64 = 1 };
+enum { DZS_CRIT_GEOMETRIC = 0, DZS_CRIT_DYNAMICAL = 1 };
 
 /* flag bits of a particle */
 enum { DZS_FL_CROSSED = 1, DZS_FL_MERGED = 2 };
@@ -68,7 +69,10 @@ enum { DZS_FL_CROSSED = 1, DZS_FL_MERGED = 2 };
 enum {
   DZS_STAGE_KICK_DRIFT = 1, /* opening kick, drift, crossing test, Morton keys, records */
   DZS_STAGE_SORT = 2,       /* stable radix sort of the keys + state permutation */
-  DZS_STAGE_MERGE = 4,      /* DZS merge against R_lc(a_step+1) (only if dzs_on) */
+  DZS_STAGE_MERGE = 4,      /* DZS merge against R_lc(a_step+1) (only if dzs_on); the
+                               dynamical criterion takes a_min from the kick-drift stage
+                               of the same step (DZS_ESTATE if the state was sorted
+                               since its accelerations were computed without one) */
   DZS_STAGE_FORCE = 8,      /* tree build, PM, tree walk: g of the current particles */
   DZS_STAGE_CLOSE = 16,     /* closing kick p += g K(a_step+1/2, a_step+1) */
   DZS_STAGE_ALL = 31
@@ -102,6 +106,12 @@ typedef struct {
   int32_t precision;    /* DZS_FP32 | DZS_FP64 force arithmetic */
   int32_t device;       /* CUDA device ordinal */
   uint64_t lc_capacity; /* lightcone ring records; 0 = N0 (never overflows) */
+  int32_t dzs_criterion; /* DZS_CRIT_GEOMETRIC: l/D < theta_dzs (Sec. 2.2.1);
+                           DZS_CRIT_DYNAMICAL: Eq. 2 with d -> D of Eq. 3 */
+  int32_t reserved_;     /* must be 0 */
+  double alpha_dyn;      /* dynamical: merge iff D > 0 and G M l^2 / D^4 <
+                            alpha_dyn a_min, a_min = smallest |g| (previous
+                            step) of the particles not yet crossed; >= 0 */
 } dzs_params;
 
 /* one lightcone record: particle id and multiplicity, crossing expansion
@@ -174,11 +184,26 @@ DZS_API dzs_status dzs_accel(dzs_ctx* c, int32_t parts, double* g_out);
 
 /* Run the DZS merge alone (paper Sec. 2.2) on the current state, which must
  * be Morton-sorted, against the lattice lightcone radius rlat
- * (R_lc / L * 2^32). */
+ * (R_lc / L * 2^32).  With DZS_CRIT_DYNAMICAL, a_min is taken from the
+ * state's accelerations g of the particles whose CROSSED flag is clear
+ * (infinite when there is none). */
 DZS_API dzs_status dzs_merge_only(dzs_ctx* c, uint64_t rlat);
 
 /* Sum k, Sum k p[3], Sum k x[3] (Mpc/h), N (FP64; integer sums exact). */
 DZS_API dzs_status dzs_diagnostics(dzs_ctx* c, double out[8]);
+
+/* Checkpoint / restore (adapts the paper's halt-and-restart, Sec. 4.1.1: a run
+ * stopped to re-allocate resources resumes from its output).  The
+ * checkpoint holds the parameters, the step index, the particle state in the
+ * context's own precision (raw, so a restored run continues bit for bit) and
+ * the lightcone records not yet drained.  dzs_checkpoint_bytes gives the size;
+ * dzs_checkpoint writes it to caller-owned host memory (DZS_EINVAL if cap is
+ * too small); dzs_restore loads it into a context created with the same
+ * parameters (device and lc_capacity may differ), DZS_EINVAL if the blob is
+ * malformed or the parameters differ.  All three synchronise. */
+DZS_API dzs_status dzs_checkpoint_bytes(dzs_ctx* c, size_t* bytes);
+DZS_API dzs_status dzs_checkpoint(dzs_ctx* c, void* host_buf, size_t cap, size_t* written);
+DZS_API dzs_status dzs_restore(dzs_ctx* c, const void* host_buf, size_t len);
 
 /* The context's FP64 tables: a[nsteps+1], drift[nsteps], kick1[nsteps]
  * (a_n -> a_n+1/2), kick2[nsteps] (a_n+1/2 -> a_n+1), rlc[nsteps+1] (Mpc/h),

@@ -23,6 +23,7 @@ STATUS_NAMES = ["DZS_OK", "DZS_EINVAL", "DZS_ENOMEM", "DZS_ECUDA", "DZS_EOVERFLO
                 "DZS_ESTATE", "DZS_EDEVICE"]
 RLC_SWEEP, RLC_PHYSICAL = 0, 1
 FP32, FP64 = 0, 1
+CRIT_GEOMETRIC, CRIT_DYNAMICAL = 0, 1
 FL_CROSSED, FL_MERGED = 1, 2
 STAGE_KICK_DRIFT, STAGE_SORT, STAGE_MERGE, STAGE_FORCE, STAGE_CLOSE, STAGE_ALL = 1, 2, 4, 8, 16, 31
 ACC_PM, ACC_TREE, ACC_ALL = 1, 2, 3
@@ -32,7 +33,8 @@ EXPORTED = ["dzs_params_default", "dzs_footprint_bytes", "dzs_create", "dzs_ics"
             "dzs_run_stages", "dzs_lightcone_drain", "dzs_destroy", "dzs_get_count", "dzs_get_state",
             "dzs_set_state", "dzs_accel", "dzs_merge_only", "dzs_diagnostics", "dzs_get_tables",
             "dzs_get_mesh", "dzs_get_counters", "dzs_set_profiling", "dzs_get_profile",
-            "dzs_morton_sort_noalloc", "dzs_last_error"]
+            "dzs_morton_sort_noalloc", "dzs_checkpoint_bytes", "dzs_checkpoint", "dzs_restore",
+            "dzs_last_error"]
 NOALLOC_SORT_MAX_N = 262144
 PROF_NAMES = ["kick_drift", "sort", "merge", "tree", "pm", "walk"]
 
@@ -47,7 +49,8 @@ class Params(C.Structure):
         ("rs_cells", C.c_double), ("rcut_rs", C.c_double), ("theta", C.c_double),
         ("soft_frac", C.c_double), ("theta_dzs", C.c_double), ("buffer_cells", C.c_double),
         ("seed", C.c_uint64), ("precision", C.c_int32), ("device", C.c_int32),
-        ("lc_capacity", C.c_uint64),
+        ("lc_capacity", C.c_uint64), ("dzs_criterion", C.c_int32), ("reserved_", C.c_int32),
+        ("alpha_dyn", C.c_double),
     ]
 
 
@@ -85,6 +88,8 @@ def load(path: str = LIB_PATH):
         "dzs_accel": [vp, i32, vp], "dzs_merge_only": [vp, u64], "dzs_diagnostics": [vp, vp],
         "dzs_get_tables": [vp, vp, vp, vp, vp, vp, vp], "dzs_get_mesh": [vp, i32, vp],
         "dzs_get_counters": [vp, vp], "dzs_set_profiling": [vp, i32], "dzs_get_profile": [vp, vp, vp],
+        "dzs_checkpoint_bytes": [vp, C.POINTER(sz)], "dzs_checkpoint": [vp, vp, sz, C.POINTER(sz)],
+        "dzs_restore": [vp, vp, sz],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -241,6 +246,20 @@ def dzs_morton_sort_noalloc(d_u: int, n: int, d_perm: int, d_keys: int = 0, stre
                                           C.c_void_p(d_keys) if d_keys else None, C.c_void_p(stream))
 
 
+def dzs_checkpoint(h) -> bytes:
+    nb = C.c_size_t(0)
+    _check(load().dzs_checkpoint_bytes(h, C.byref(nb)), h)
+    buf = np.zeros(nb.value, np.uint8)
+    w = C.c_size_t(0)
+    _check(load().dzs_checkpoint(h, _ptr(buf), nb.value, C.byref(w)), h)
+    return buf[:w.value].tobytes()
+
+
+def dzs_restore(h, blob: bytes):
+    buf = np.frombuffer(blob, np.uint8)
+    _check(load().dzs_restore(h, _ptr(buf), len(buf)), h)
+
+
 class Context:
     """Owns one dzs_ctx; methods mirror the C entry points."""
 
@@ -280,3 +299,5 @@ class Context:
     def counters(self): return dzs_get_counters(self.h)
     def set_profiling(self, on=True): dzs_set_profiling(self.h, on)
     def profile(self): return dzs_get_profile(self.h)
+    def checkpoint(self): return dzs_checkpoint(self.h)
+    def restore(self, blob): dzs_restore(self.h, blob)

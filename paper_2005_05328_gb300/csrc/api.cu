@@ -44,6 +44,9 @@ const char* validate(const dzs_params* p) {
   if (!(p->buffer_cells >= 0)) return "buffer_cells must be >= 0";
   if (p->rlc_mode != DZS_RLC_SWEEP && p->rlc_mode != DZS_RLC_PHYSICAL) return "unknown rlc_mode";
   if (p->precision != DZS_FP32 && p->precision != DZS_FP64) return "unknown precision";
+  if (p->dzs_criterion != DZS_CRIT_GEOMETRIC && p->dzs_criterion != DZS_CRIT_DYNAMICAL) return "unknown dzs_criterion";
+  if (!(p->alpha_dyn >= 0)) return "alpha_dyn must be >= 0";
+  if (p->reserved_ != 0) return "reserved_ must be 0";
   return nullptr;
 }
 
@@ -265,6 +268,8 @@ dzs_status dzs_params_default(dzs_params* p) {
   p->precision = DZS_FP32;
   p->device = 0;
   p->lc_capacity = 0;
+  p->dzs_criterion = DZS_CRIT_GEOMETRIC;
+  p->alpha_dyn = 0.01;
   return DZS_OK;
 }
 
@@ -427,6 +432,8 @@ dzs_status dzs_ics(dzs_ctx* c) {
   launch_sort(c);
   run_force(c, DZS_ACC_ALL, false);
   c->have_state = true;
+  c->g_aligned = true;
+  c->amin2_ready = false;
   CK(cudaGetLastError());
   return check_device_errors(c);
 }
@@ -442,23 +449,37 @@ dzs_status dzs_run_stages(dzs_ctx* c, uint32_t mask) {
     ProfScope ps(c, DZS_PROF_KICK_DRIFT);
     launch_kick_drift(c, st, true, true);
     launch_records(c, st);
+    // a_min of the dynamical criterion: the accelerations the particles were
+    // just kicked with, restricted to those not crossed after this drift
+    if (c->P.dzs_on && c->P.dzs_criterion == DZS_CRIT_DYNAMICAL) launch_amin2(c);
   }
   if (mask & DZS_STAGE_SORT) {
     ProfScope ps(c, DZS_PROF_SORT);
     if (!(mask & DZS_STAGE_KICK_DRIFT)) launch_keys(c);
     launch_sort(c);
+    c->g_aligned = false;  // the sort permutes the state but not g
   }
   if ((mask & DZS_STAGE_MERGE) && c->P.dzs_on) {
     ProfScope ps(c, DZS_PROF_MERGE);
+    if (c->P.dzs_criterion == DZS_CRIT_DYNAMICAL && !c->amin2_ready) {
+      if (!c->g_aligned)
+        return fail(c, DZS_ESTATE, "dynamical criterion: a_min needs the kick-drift stage before the sort");
+      launch_amin2(c);
+    }
     launch_merge(c, c->T.rlat[st + 1]);
+    c->g_aligned = false;  // the merge compacts the state but not g
   }
   if (mask & DZS_STAGE_FORCE) {
     run_force(c, DZS_ACC_ALL, (mask & DZS_STAGE_CLOSE) != 0);
+    c->g_aligned = true;
   } else if (mask & DZS_STAGE_CLOSE) {
     ProfScope ps(c, DZS_PROF_WALK);
     launch_close_kick(c, st);
   }
-  if (mask & DZS_STAGE_CLOSE) c->step = st + 1;
+  if (mask & DZS_STAGE_CLOSE) {
+    c->step = st + 1;
+    c->amin2_ready = false;
+  }
   CK(cudaGetLastError());
   return DZS_OK;
 }
@@ -576,6 +597,8 @@ dzs_status dzs_set_state(dzs_ctx* c, const uint32_t* u, const double* p, const d
   CK(cudaMemset(c->B.counters + 12, 0, 2 * sizeof(uint64_t)));  // node tests, rounds
   c->step = step;
   c->have_state = true;
+  c->g_aligned = true;
+  c->amin2_ready = false;
   if (g) {
     for (int ax = 0; ax < 3; ++ax)
       CK(cudaMemcpy(conv + ax * c->cap, g + ax * n, 8 * n, cudaMemcpyHostToDevice));
@@ -615,8 +638,13 @@ dzs_status dzs_merge_only(dzs_ctx* c, uint64_t rlat) {
   dzs_status s = guard(c);
   if (s) return s;
   if (!c->have_state) return fail(c, DZS_ESTATE, "no particle state");
+  if (c->P.dzs_criterion == DZS_CRIT_DYNAMICAL) {
+    if (!c->g_aligned) return fail(c, DZS_ESTATE, "dynamical criterion: g is not in the state's order");
+    launch_amin2(c);
+  }
   launch_keys(c);
   launch_merge(c, rlat);
+  c->g_aligned = false;
   CK(cudaGetLastError());
   return check_device_errors(c);
 }
@@ -630,6 +658,126 @@ dzs_status dzs_diagnostics(dzs_ctx* c, double out[8]) {
   s = check_device_errors(c);
   if (s) return s;
   CK(cudaMemcpy(out, c->B.diag, 8 * sizeof(double), cudaMemcpyDeviceToHost));
+  return DZS_OK;
+}
+
+// ---- checkpoint / restore: header, raw state arrays in the context's own
+// precision (no conversion, so a restored run continues bit for bit), and the
+// lightcone records not yet drained
+namespace {
+constexpr uint64_t kCkptMagic = 0x315450434b535a44ull;  // "DZSKCPT1"
+struct CkptHeader {
+  uint64_t magic;
+  uint64_t bytes;
+  dzs_params params;
+  uint64_t n, step, pending, dropped, rsz;
+};
+size_t ckpt_size(const dzs_ctx* c, uint64_t n, uint64_t pending) {
+  size_t rsz = c->fp64 ? 8 : 4;
+  return sizeof(CkptHeader) + n * (12 + 6 * rsz + 4 + 4 + 1) + pending * sizeof(dzs_lc_record);
+}
+bool same_physics(const dzs_params& a, const dzs_params& b) {
+  dzs_params x = a, y = b;
+  x.device = y.device = 0;
+  x.lc_capacity = y.lc_capacity = 0;
+  return memcmp(&x, &y, sizeof x) == 0;
+}
+}  // namespace
+
+dzs_status dzs_checkpoint_bytes(dzs_ctx* c, size_t* bytes) {
+  size_t n = 0;
+  dzs_status s = dzs_get_count(c, &n, nullptr);
+  if (s) return s;
+  if (!bytes) return fail(c, DZS_EINVAL, "bytes is NULL");
+  uint64_t head = 0;
+  CK(cudaMemcpy(&head, c->B.counters, sizeof head, cudaMemcpyDeviceToHost));
+  *bytes = ckpt_size(c, n, head - c->drained);
+  return DZS_OK;
+}
+
+dzs_status dzs_checkpoint(dzs_ctx* c, void* host_buf, size_t cap, size_t* written) {
+  size_t n = 0;
+  dzs_status s = dzs_get_count(c, &n, nullptr);
+  if (s) return s;
+  if (!c->have_state) return fail(c, DZS_ESTATE, "no particle state");
+  uint64_t ctr[2];
+  CK(cudaMemcpy(ctr, c->B.counters, sizeof ctr, cudaMemcpyDeviceToHost));
+  const uint64_t pending = ctr[0] - c->drained;
+  const size_t need = ckpt_size(c, n, pending), rsz = c->fp64 ? 8 : 4;
+  if (written) *written = 0;
+  if (!host_buf || cap < need) return fail(c, DZS_EINVAL, "checkpoint buffer too small");
+  char* o = (char*)host_buf;
+  CkptHeader h;
+  memset(&h, 0, sizeof h);
+  h.magic = kCkptMagic;
+  h.bytes = need;
+  h.params = c->P;
+  h.n = n;
+  h.step = (uint64_t)c->step;
+  h.pending = pending;
+  h.dropped = ctr[1];
+  h.rsz = rsz;
+  memcpy(o, &h, sizeof h);
+  o += sizeof h;
+  for (int ax = 0; ax < 3; ++ax, o += 4 * n) CK(cudaMemcpy(o, c->B.u + ax * c->cap, 4 * n, cudaMemcpyDeviceToHost));
+  for (int ax = 0; ax < 3; ++ax, o += rsz * n)
+    CK(cudaMemcpy(o, (char*)c->B.p + ax * c->cap * rsz, rsz * n, cudaMemcpyDeviceToHost));
+  for (int ax = 0; ax < 3; ++ax, o += rsz * n)
+    CK(cudaMemcpy(o, (char*)c->B.g + ax * c->cap * rsz, rsz * n, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(o, c->B.k, 4 * n, cudaMemcpyDeviceToHost));
+  o += 4 * n;
+  CK(cudaMemcpy(o, c->B.id, 4 * n, cudaMemcpyDeviceToHost));
+  o += 4 * n;
+  CK(cudaMemcpy(o, c->B.fl, n, cudaMemcpyDeviceToHost));
+  o += n;
+  for (uint64_t done = 0; done < pending;) {
+    uint64_t slot = (c->drained + done) % c->ring_cap, chunk = c->ring_cap - slot;
+    if (chunk > pending - done) chunk = pending - done;
+    CK(cudaMemcpy(o, c->B.ring + slot, chunk * sizeof(dzs_lc_record), cudaMemcpyDeviceToHost));
+    o += chunk * sizeof(dzs_lc_record);
+    done += chunk;
+  }
+  if (written) *written = need;
+  return DZS_OK;
+}
+
+dzs_status dzs_restore(dzs_ctx* c, const void* host_buf, size_t len) {
+  dzs_status s = guard(c);
+  if (s) return s;
+  CkptHeader h;
+  if (!host_buf || len < sizeof h) return fail(c, DZS_EINVAL, "checkpoint too short");
+  memcpy(&h, host_buf, sizeof h);
+  const size_t rsz = c->fp64 ? 8 : 4;
+  if (h.magic != kCkptMagic || h.rsz != rsz) return fail(c, DZS_EINVAL, "not a checkpoint of this precision");
+  if (!same_physics(h.params, c->P)) return fail(c, DZS_EINVAL, "checkpoint parameters differ from the context's");
+  if (h.n > (uint64_t)c->cap || h.step > (uint64_t)c->P.nsteps || h.pending > c->ring_cap ||
+      h.bytes != ckpt_size(c, h.n, h.pending) || len < h.bytes)
+    return fail(c, DZS_EINVAL, "inconsistent checkpoint");
+  CK(cudaStreamSynchronize(c->stream));
+  const size_t n = h.n;
+  const char* o = (const char*)host_buf + sizeof h;
+  for (int ax = 0; ax < 3; ++ax, o += 4 * n) CK(cudaMemcpy(c->B.u + ax * c->cap, o, 4 * n, cudaMemcpyHostToDevice));
+  for (int ax = 0; ax < 3; ++ax, o += rsz * n)
+    CK(cudaMemcpy((char*)c->B.p + ax * c->cap * rsz, o, rsz * n, cudaMemcpyHostToDevice));
+  for (int ax = 0; ax < 3; ++ax, o += rsz * n)
+    CK(cudaMemcpy((char*)c->B.g + ax * c->cap * rsz, o, rsz * n, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(c->B.k, o, 4 * n, cudaMemcpyHostToDevice));
+  o += 4 * n;
+  CK(cudaMemcpy(c->B.id, o, 4 * n, cudaMemcpyHostToDevice));
+  o += 4 * n;
+  CK(cudaMemcpy(c->B.fl, o, n, cudaMemcpyHostToDevice));
+  o += n;
+  if (h.pending) CK(cudaMemcpy(c->B.ring, o, h.pending * sizeof(dzs_lc_record), cudaMemcpyHostToDevice));
+  uint64_t ctr[2] = {h.pending, h.dropped};
+  CK(cudaMemcpy(c->B.counters, ctr, sizeof ctr, cudaMemcpyHostToDevice));
+  int32_t nn = (int32_t)n;
+  CK(cudaMemcpy(c->B.n, &nn, sizeof nn, cudaMemcpyHostToDevice));
+  CK(cudaMemset(c->B.err, 0, 16));
+  c->drained = 0;
+  c->step = (int32_t)h.step;
+  c->have_state = true;
+  c->g_aligned = true;
+  c->amin2_ready = false;
   return DZS_OK;
 }
 

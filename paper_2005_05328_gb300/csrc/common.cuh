@@ -154,6 +154,11 @@ struct dzs_ctx {
   int32_t step = 0;
   bool have_state = false;
   bool poisoned = false;
+  // dynamical DZS criterion: g is in the particles' current order (false
+  // between a step's sort and its force stage), and a_min^2 of this step
+  // has been reduced into counters[14] (after the kick-drift stage)
+  bool g_aligned = true;
+  bool amin2_ready = false;
   uint64_t drained = 0;
   size_t ring_cap = 0;
   char* arena = nullptr;
@@ -187,6 +192,7 @@ void launch_keys(dzs_ctx* c);
 void launch_unpermute(dzs_ctx* c, double* g_out);
 void launch_close_kick(dzs_ctx* c, int step);
 void launch_merge(dzs_ctx* c, uint64_t rlat);
+void launch_amin2(dzs_ctx* c);
 void launch_tree(dzs_ctx* c);
 void launch_pm(dzs_ctx* c, bool want_pm);
 void launch_walk(dzs_ctx* c, bool tree, bool close_kick, int step);

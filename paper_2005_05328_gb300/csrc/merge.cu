@@ -14,6 +14,17 @@
 // The first member of a merged cell becomes the new particle (mass K, integer
 // COM rounded half up, p = (sum k p) / K summed left to right in FP64,
 // id = min id); the others are dropped by a stable compaction.
+//
+// Dynamical criterion (Sec. 2.2.1: Eq. 2 with d replaced by D_n of Eq. 3 and
+// |a_old| by the smallest |a| of the particles not yet crossed): merge iff
+//     D > 0  and  G M l_j^2 / D^4 < alpha a_min,
+//     D = (sqrt(d_COM^2) - (R_lat + b_lat)) L / 2^32,
+// every operation a correctly rounded FP64 intrinsic in that order, so the
+// decision equals a plain IEEE evaluation bit for bit.  a_min^2 is reduced
+// on the device just before the mark pass from the accelerations the state
+// carries (the previous step's forces) and the crossing flags of this step.
+#include <cmath>
+
 #include "common.cuh"
 
 namespace dzs {
@@ -25,8 +36,57 @@ struct MergeParams {
   uint64_t thr[kMaxLevel + 1];  // T_j (UINT64_MAX: level never merges)
   uint64_t rb2;                 // (R_lat + b_lat)^2: members must lie beyond
   int jmin;
-  int filter;                   // 1 when theta_dzs <= 1/sqrt(3)
+  int filter;                   // 1 when theta_dzs <= 1/sqrt(3) (geometric only)
+  int criterion;                // DZS_CRIT_GEOMETRIC / DZS_CRIT_DYNAMICAL
+  double rb;                    // R_lat + b_lat (dynamical)
+  double scale;                 // L / 2^32
+  double gm0;                   // G m0 = 1.5 Omega_m L^3 / (4 pi N0)
+  double alpha;                 // alpha of Eq. 2
+  double l2[kMaxLevel + 1];     // (L / 2^j)^2
+  const uint64_t* amin2_slot;   // ~bits of a_min^2 (0: no particle inside)
 };
+
+// a_min^2 = min over particles not yet crossed of |g|^2, FP64 without
+// contraction.  Non-negative doubles order like their bit patterns, so the
+// minimum is an integer max over the complemented bits (slot zeroed before).
+template <class R>
+__global__ void k_amin2(const int32_t* __restrict__ d_n, int64_t cap, const R* __restrict__ g,
+                        const uint8_t* __restrict__ fl, unsigned long long* __restrict__ slot) {
+  const int64_t n = *d_n;
+  unsigned long long best = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (fl[i] & kFlCrossed) continue;
+    double gx = (double)g[i], gy = (double)g[cap + i], gz = (double)g[2 * cap + i];
+    double a2 = __dadd_rn(__dadd_rn(__dmul_rn(gx, gx), __dmul_rn(gy, gy)), __dmul_rn(gz, gz));
+    if (!(a2 == a2)) continue;  // NaN never wins the minimum
+    unsigned long long c = ~(unsigned long long)__double_as_longlong(a2);
+    best = c > best ? c : best;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long t = __shfl_down_sync(0xffffffffu, best, o);
+    best = t > best ? t : best;
+  }
+  __shared__ unsigned long long wbest[32];
+  if ((threadIdx.x & 31) == 0) wbest[threadIdx.x >> 5] = best;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    best = threadIdx.x < (blockDim.x >> 5) ? wbest[threadIdx.x] : 0ull;
+    for (int o = 16; o > 0; o >>= 1) {
+      unsigned long long t = __shfl_down_sync(0xffffffffu, best, o);
+      best = t > best ? t : best;
+    }
+    if (threadIdx.x == 0 && best) atomicMax(slot, best);  // one atomic per block
+  }
+}
+
+__device__ __forceinline__ bool dynamical_merge(const MergeParams& mp, uint64_t d2, uint64_t K, int j,
+                                                double rhs) {
+  double D = __dmul_rn(__dsub_rn(__dsqrt_rn((double)d2), mp.rb), mp.scale);
+  if (!(D > 0.0)) return false;
+  double D2 = __dmul_rn(D, D);
+  double lhs = __ddiv_rn(__dmul_rn(__dmul_rn(mp.gm0, (double)K), mp.l2[j]), __dmul_rn(D2, D2));
+  return lhs < rhs;
+}
 
 // ---- 4-channel uint64 exclusive prefix sums: k, k ux, k uy, k uz
 __global__ void k_prefix_totals(const int32_t* __restrict__ d_n, int64_t cap, const uint32_t* __restrict__ u,
@@ -158,6 +218,12 @@ __global__ void k_merge_mark(const int32_t* __restrict__ d_n, int64_t cap, const
   const int64_t n = *d_n;
   const uint64_t* PK = pre;
   const uint64_t* PS = pre + (cap + 1);
+  double rhs = 0.0;  // alpha a_min (dynamical)
+  if (mp.criterion == DZS_CRIT_DYNAMICAL) {
+    uint64_t c = *mp.amin2_slot;
+    double amin2 = c ? __longlong_as_double((long long)~c) : __longlong_as_double(0x7ff0000000000000ll);
+    rhs = __dmul_rn(mp.alpha, __dsqrt_rn(amin2));
+  }
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     int32_t res = 0;
     bool cand = true;
@@ -173,7 +239,7 @@ __global__ void k_merge_mark(const int32_t* __restrict__ d_n, int64_t cap, const
         lo = s;
         hi = e;
         if (e - s < 2) break;  // no finer cell holds two particles
-        if (j < mp.jmin || mp.thr[j] == ~0ull) continue;
+        if (j < mp.jmin || (mp.criterion == DZS_CRIT_GEOMETRIC && mp.thr[j] == ~0ull)) continue;
         uint64_t K = PK[e] - PK[s];
         uint64_t d2 = 0;
         for (int ax = 0; ax < 3; ++ax) {
@@ -182,8 +248,14 @@ __global__ void k_merge_mark(const int32_t* __restrict__ d_n, int64_t cap, const
           int64_t off = (int32_t)(com - 0x80000000u);
           d2 += (uint64_t)(off * off);
         }
-        uint64_t T = mp.thr[j];
-        if (d2 > T * T) {
+        bool merge;
+        if (mp.criterion == DZS_CRIT_DYNAMICAL) {
+          merge = dynamical_merge(mp, d2, K, j, rhs);
+        } else {
+          uint64_t T = mp.thr[j];
+          merge = d2 > T * T;
+        }
+        if (merge) {
           res = (s == i) ? (int32_t)e : -1;
           break;
         }
@@ -244,8 +316,23 @@ __global__ void k_merge_write(const int32_t* __restrict__ d_n, int64_t cap, cons
 
 }  // namespace
 
+void launch_amin2(dzs_ctx* c) {
+  c->launches += 1;
+  Buffers& B = c->B;
+  unsigned long long* slot = (unsigned long long*)(B.counters + 14);
+  cudaMemsetAsync(slot, 0, sizeof(uint64_t), c->stream);
+  int grid = grid_for(c->N0);
+  if (c->fp64)
+    k_amin2<double><<<grid, kThreads, 0, c->stream>>>(B.n, c->cap, (const double*)B.g, B.fl, slot);
+  else
+    k_amin2<float><<<grid, kThreads, 0, c->stream>>>(B.n, c->cap, (const float*)B.g, B.fl, slot);
+  c->amin2_ready = true;
+}
+
+// the dynamical criterion reads a_min^2 from counters[14] (launch_amin2 first)
 void launch_merge(dzs_ctx* c, uint64_t rlat) {
   c->launches += 8;
+  const bool dyn = c->P.dzs_criterion == DZS_CRIT_DYNAMICAL;
   Buffers& B = c->B;
   MergeParams mp;
   for (int j = 0; j <= kMaxLevel; ++j)
@@ -255,7 +342,18 @@ void launch_merge(dzs_ctx* c, uint64_t rlat) {
   uint64_t rb = rlat + c->blat;
   mp.rb2 = (rb >= 4294967296ull) ? ~0ull : rb * rb;
   mp.jmin = c->jmin;
-  mp.filter = (c->P.theta_dzs <= 0.5773502691896257) ? 1 : 0;
+  mp.filter = (!dyn && c->P.theta_dzs <= 0.5773502691896257) ? 1 : 0;
+  mp.criterion = c->P.dzs_criterion;
+  mp.rb = (double)rb;
+  mp.scale = c->scale;
+  mp.gm0 = c->gm0;
+  mp.alpha = c->P.alpha_dyn;
+  for (int j = 0; j <= kMaxLevel; ++j) {
+    double l = std::ldexp(c->P.box, -j);
+    mp.l2[j] = l * l;
+  }
+  uint64_t* slot = c->B.counters + 14;
+  mp.amin2_slot = slot;
   int nchunks = (int)((c->cap + kChunk) / kChunk);
   uint64_t* tot = (uint64_t*)B.blocksum;
   k_prefix_totals<<<nchunks, 256, 0, c->stream>>>(B.n, c->cap, B.u, B.k, tot);
