@@ -112,6 +112,10 @@ typedef struct {
   double alpha_dyn;      /* dynamical: merge iff D > 0 and G M l^2 / D^4 <
                             alpha_dyn a_min, a_min = smallest |g| (previous
                             step) of the particles not yet crossed; >= 0 */
+  uint64_t capacity;     /* particle slots of the context, <= N0; 0 = N0.  dzs_ics
+                            needs N0; a smaller context takes a restored or
+                            injected state of up to `capacity` particles (the
+                            re-allocation after a halt, dzs_step_until) */
 } dzs_params;
 
 /* one lightcone record: particle id and multiplicity, crossing expansion
@@ -208,6 +212,32 @@ DZS_API dzs_status dzs_restore(dzs_ctx* c, const void* host_buf, size_t len);
 /* The context's FP64 tables: a[nsteps+1], drift[nsteps], kick1[nsteps]
  * (a_n -> a_n+1/2), kick2[nsteps] (a_n+1/2 -> a_n+1), rlc[nsteps+1] (Mpc/h),
  * rlat[nsteps+1].  Any pointer may be NULL. */
+/* Halt criteria (adapted from Sec. 4.1.1: the run stops for a re-allocation
+ * of resources).  On one GPU the per-task workload balance has no
+ * counterpart; the particle ratio R = N / N0 and the run-time rule do. */
+typedef struct {
+  double ratio_min;    /* halt once R < ratio_min (0: never) */
+  double wall_limit_s; /* run-time limit of this call in seconds (0: none) */
+  double horizon_s;    /* at the limit, halt for re-allocation if R, extrapolated
+                          linearly in wall time, falls below ratio_min within
+                          horizon_s after the restart */
+} dzs_halt;
+
+enum {
+  DZS_HALT_NONE = 0,     /* max_steps done or a = 1 reached */
+  DZS_HALT_RATIO = 1,    /* R < ratio_min */
+  DZS_HALT_PREDICTED = 2, /* wall limit reached, R predicted below ratio_min within horizon_s */
+  DZS_HALT_WALL = 3      /* wall limit reached, no re-allocation predicted */
+};
+
+/* Run up to max_steps full steps, checking the criteria after each step (one
+ * synchronisation per step).  *reason gets a DZS_HALT_* value, *ratio the
+ * last R.  A halted run resumes with dzs_step / dzs_step_until, or through
+ * dzs_checkpoint and dzs_restore into a context created with a smaller
+ * `capacity` (the freed memory goes back to the device). */
+DZS_API dzs_status dzs_step_until(dzs_ctx* c, int32_t max_steps, const dzs_halt* h, int32_t* steps_done,
+                                  int32_t* reason, double* ratio);
+
 DZS_API dzs_status dzs_get_tables(dzs_ctx* c, double* a, double* drift, double* kick1, double* kick2,
                           double* rlc, uint64_t* rlat);
 

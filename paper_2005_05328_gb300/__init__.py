@@ -34,7 +34,7 @@ EXPORTED = ["dzs_params_default", "dzs_footprint_bytes", "dzs_create", "dzs_ics"
             "dzs_set_state", "dzs_accel", "dzs_merge_only", "dzs_diagnostics", "dzs_get_tables",
             "dzs_get_mesh", "dzs_get_counters", "dzs_set_profiling", "dzs_get_profile",
             "dzs_morton_sort_noalloc", "dzs_checkpoint_bytes", "dzs_checkpoint", "dzs_restore",
-            "dzs_last_error"]
+            "dzs_step_until", "dzs_last_error"]
 NOALLOC_SORT_MAX_N = 262144
 PROF_NAMES = ["kick_drift", "sort", "merge", "tree", "pm", "walk"]
 
@@ -50,8 +50,15 @@ class Params(C.Structure):
         ("soft_frac", C.c_double), ("theta_dzs", C.c_double), ("buffer_cells", C.c_double),
         ("seed", C.c_uint64), ("precision", C.c_int32), ("device", C.c_int32),
         ("lc_capacity", C.c_uint64), ("dzs_criterion", C.c_int32), ("reserved_", C.c_int32),
-        ("alpha_dyn", C.c_double),
+        ("alpha_dyn", C.c_double), ("capacity", C.c_uint64),
     ]
+
+
+class Halt(C.Structure):
+    _fields_ = [("ratio_min", C.c_double), ("wall_limit_s", C.c_double), ("horizon_s", C.c_double)]
+
+
+HALT_NONE, HALT_RATIO, HALT_PREDICTED, HALT_WALL = 0, 1, 2, 3
 
 
 RECORD_DTYPE = np.dtype([("id", "<u4"), ("k", "<u4"), ("a_cross", "<f8"),
@@ -90,6 +97,7 @@ def load(path: str = LIB_PATH):
         "dzs_get_counters": [vp, vp], "dzs_set_profiling": [vp, i32], "dzs_get_profile": [vp, vp, vp],
         "dzs_checkpoint_bytes": [vp, C.POINTER(sz)], "dzs_checkpoint": [vp, vp, sz, C.POINTER(sz)],
         "dzs_restore": [vp, vp, sz],
+        "dzs_step_until": [vp, i32, C.POINTER(Halt), C.POINTER(i32), C.POINTER(i32), C.POINTER(C.c_double)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -260,6 +268,14 @@ def dzs_restore(h, blob: bytes):
     _check(load().dzs_restore(h, _ptr(buf), len(buf)), h)
 
 
+def dzs_step_until(h, max_steps: int, ratio_min=0.0, wall_limit_s=0.0, horizon_s=0.0):
+    """-> (steps done, DZS_HALT_* reason, last N / N0)"""
+    hp = Halt(ratio_min, wall_limit_s, horizon_s)
+    done, why, r = C.c_int32(0), C.c_int32(0), C.c_double(0)
+    _check(load().dzs_step_until(h, max_steps, C.byref(hp), C.byref(done), C.byref(why), C.byref(r)), h)
+    return done.value, why.value, r.value
+
+
 class Context:
     """Owns one dzs_ctx; methods mirror the C entry points."""
 
@@ -301,3 +317,4 @@ class Context:
     def profile(self): return dzs_get_profile(self.h)
     def checkpoint(self): return dzs_checkpoint(self.h)
     def restore(self, blob): dzs_restore(self.h, blob)
+    def step_until(self, max_steps, **halt): return dzs_step_until(self.h, max_steps, **halt)

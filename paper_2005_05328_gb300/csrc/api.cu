@@ -3,6 +3,7 @@
 // diagnostics.  Step order (paper Sec. 2.2: DZS on global steps, tree rebuilt
 // and forces recomputed after a merge): opening kick + drift + crossing ->
 // records -> Morton sort -> merge -> tree -> PM -> walk + closing kick.
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -47,6 +48,7 @@ const char* validate(const dzs_params* p) {
   if (p->dzs_criterion != DZS_CRIT_GEOMETRIC && p->dzs_criterion != DZS_CRIT_DYNAMICAL) return "unknown dzs_criterion";
   if (!(p->alpha_dyn >= 0)) return "alpha_dyn must be >= 0";
   if (p->reserved_ != 0) return "reserved_ must be 0";
+  if (p->capacity > (uint64_t)p->n1d * p->n1d * p->n1d) return "capacity exceeds n1d^3";
   return nullptr;
 }
 
@@ -85,7 +87,7 @@ struct Plan {
       o_cstart, o_tw, o_green, o_ring, o_n, o_err, o_counters, o_diag, o_convert;
   size_t total;
   explicit Plan(const dzs_params& P) {
-    cap = (int64_t)P.n1d * P.n1d * P.n1d;
+    cap = P.capacity ? (int64_t)P.capacity : (int64_t)P.n1d * P.n1d * P.n1d;
     node_cap = 2 * cap + 1024;
     m3 = (int64_t)P.mesh * P.mesh * P.mesh;
     nspec = (int64_t)P.mesh * P.mesh * (P.mesh / 2 + 1);
@@ -300,7 +302,7 @@ dzs_status dzs_create(const dzs_params* p, void* cuda_stream, dzs_ctx** out) {
   c->fp64 = p->precision == DZS_FP64;
   c->n1 = p->n1d;
   c->N0 = (int64_t)p->n1d * p->n1d * p->n1d;
-  c->cap = c->N0;
+  c->cap = p->capacity ? (int64_t)p->capacity : c->N0;
   c->M = p->mesh;
   c->logM = ilog2i(p->mesh);
   c->lat = 4294967296.0 / p->box;
@@ -423,6 +425,7 @@ dzs_status dzs_destroy(dzs_ctx* c) {
 dzs_status dzs_ics(dzs_ctx* c) {
   dzs_status s = guard(c);
   if (s) return s;
+  if (c->cap != c->N0) return fail(c, DZS_EINVAL, "dzs_ics needs capacity n1d^3");
   CK(cudaMemsetAsync(c->B.counters, 0, 8 * 16, c->stream));
   CK(cudaMemsetAsync(c->B.err, 0, 16, c->stream));
   c->drained = 0;
@@ -496,6 +499,48 @@ dzs_status dzs_step(dzs_ctx* c, int32_t nsteps, int32_t* steps_done) {
     ++done;
   }
   if (steps_done) *steps_done = done;
+  return DZS_OK;
+}
+
+dzs_status dzs_step_until(dzs_ctx* c, int32_t max_steps, const dzs_halt* h, int32_t* steps_done,
+                          int32_t* reason, double* ratio) {
+  dzs_status s = guard(c);
+  if (s) return s;
+  if (steps_done) *steps_done = 0;
+  if (reason) *reason = DZS_HALT_NONE;
+  if (max_steps < 0 || !h || !(h->ratio_min >= 0) || !(h->wall_limit_s >= 0) || !(h->horizon_s >= 0))
+    return fail(c, DZS_EINVAL, "bad halt arguments");
+  if (!c->have_state) return fail(c, DZS_ESTATE, "no particle state");
+  using clk = std::chrono::steady_clock;
+  const clk::time_point t0 = clk::now();
+  size_t n = 0;
+  s = dzs_get_count(c, &n, nullptr);
+  if (s) return s;
+  double r0 = (double)n / (double)c->N0, r = r0;
+  if (ratio) *ratio = r;
+  int done = 0;
+  while (done < max_steps && c->step < c->P.nsteps) {
+    s = dzs_run_stages(c, DZS_STAGE_ALL);
+    if (s) return s;
+    ++done;
+    if (steps_done) *steps_done = done;
+    s = dzs_get_count(c, &n, nullptr);  // synchronises
+    if (s) return s;
+    r = (double)n / (double)c->N0;
+    if (ratio) *ratio = r;
+    if (h->ratio_min > 0 && r < h->ratio_min) {
+      if (reason) *reason = DZS_HALT_RATIO;
+      return DZS_OK;
+    }
+    const double t = std::chrono::duration<double>(clk::now() - t0).count();
+    if (h->wall_limit_s > 0 && t >= h->wall_limit_s) {
+      // linear extrapolation of R(t) over this call's steps
+      const double slope = (r - r0) / t;
+      const bool soon = h->ratio_min > 0 && r + slope * h->horizon_s < h->ratio_min;
+      if (reason) *reason = soon ? DZS_HALT_PREDICTED : DZS_HALT_WALL;
+      return DZS_OK;
+    }
+  }
   return DZS_OK;
 }
 
@@ -576,7 +621,7 @@ dzs_status dzs_set_state(dzs_ctx* c, const uint32_t* u, const double* p, const d
                          const uint32_t* id, const uint8_t* fl, size_t n, int32_t step) {
   dzs_status s = guard(c);
   if (s) return s;
-  if (n > (size_t)c->cap) return fail(c, DZS_EINVAL, "n exceeds n1d^3");
+  if (n > (size_t)c->cap) return fail(c, DZS_EINVAL, "n exceeds the context's capacity");
   if (n > 0 && (!u || !p || !k || !id || !fl)) return fail(c, DZS_EINVAL, "NULL state array");
   if (step < 0 || step > c->P.nsteps) return fail(c, DZS_EINVAL, "step out of range");
   CK(cudaStreamSynchronize(c->stream));
@@ -680,6 +725,7 @@ bool same_physics(const dzs_params& a, const dzs_params& b) {
   dzs_params x = a, y = b;
   x.device = y.device = 0;
   x.lc_capacity = y.lc_capacity = 0;
+  x.capacity = y.capacity = 0;
   return memcmp(&x, &y, sizeof x) == 0;
 }
 }  // namespace

@@ -61,3 +61,40 @@ def test_create_without_gpu_fails_cleanly(dzs):
     with pytest.raises(dzs.DzsError) as e:
         dzs.dzs_create(dzs.params())
     assert e.value.status == dzs.DZS_EDEVICE
+
+
+def test_capacity_shrinks_footprint(dzs):
+    """a context re-created after a halt with fewer particle slots holds less
+    device memory; capacity above n1d^3 is rejected"""
+    kw = dict(n1d=128, mesh=256, box=256.0, merge_level=3)
+    full = dzs.dzs_footprint_bytes(dzs.params(**kw))
+    small = dzs.dzs_footprint_bytes(dzs.params(capacity=128 ** 3 // 16, **kw))
+    assert small < full - 0.9 * (full - dzs.dzs_footprint_bytes(dzs.params(capacity=1, **kw)))
+    with pytest.raises(dzs.DzsError) as e:
+        dzs.dzs_footprint_bytes(dzs.params(capacity=128 ** 3 + 1, **kw))
+    assert e.value.status == dzs.DZS_EINVAL
+    p = dzs.params()
+    assert p.capacity == 0 and p.dzs_criterion == dzs.CRIT_GEOMETRIC and p.alpha_dyn == 0.01
+
+
+def test_struct_layouts_match_the_header(tmp_path, dzs):
+    """sizeof / offsetof of the C structs equal the ctypes mirrors"""
+    import ctypes
+    import subprocess
+    fields = [f[0] for f in dzs.Params._fields_]
+    halt = [f[0] for f in dzs.Halt._fields_]
+    body = ["#include <stdio.h>", "#include <stddef.h>", '#include "dzs.h"', "int main(void) {",
+            '  printf("%zu\\n", sizeof(dzs_params));']
+    body += ['  printf("%%zu\\n", offsetof(dzs_params, %s));' % f for f in fields]
+    body += ['  printf("%zu\\n", sizeof(dzs_halt));']
+    body += ['  printf("%%zu\\n", offsetof(dzs_halt, %s));' % f for f in halt]
+    body += ['  printf("%zu\\n", sizeof(dzs_lc_record));', "  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(body) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
+    want = [ctypes.sizeof(dzs.Params)] + [getattr(dzs.Params, f).offset for f in fields]
+    want += [ctypes.sizeof(dzs.Halt)] + [getattr(dzs.Halt, f).offset for f in halt]
+    want += [dzs.RECORD_DTYPE.itemsize]
+    assert got == want

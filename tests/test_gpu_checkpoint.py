@@ -61,3 +61,58 @@ def test_restore_rejects_mismatch(dzs):
         bad[0] ^= 0xFF
         with pytest.raises(dzs.DzsError):
             c.restore(bytes(bad))
+
+
+KW2 = dict(n1d=32, mesh=64, box=64.0, merge_level=3, seed=7)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_halt_shrink_resume_is_bit_identical(dzs, precision):
+    """Sec. 4.1.1 adapted: halt once N / N0 < 0.5, checkpoint, re-create the
+    context with only the slots the particles need, restore, finish the run;
+    state and lightcone equal those of an uninterrupted run bit for bit."""
+    with dzs.Context(**KW2, precision=precision) as ref:
+        ref.ics()
+        ref.step(96)
+        st_ref, rec_ref = ref.state(), ref.drain()
+    with dzs.Context(**KW2, precision=precision) as a:
+        a.ics()
+        done, why, r = a.step_until(96, ratio_min=0.5)
+        assert why == dzs.HALT_RATIO and r < 0.5 and 0 < done < 96
+        n, step = a.count()
+        assert step == done and n / 32 ** 3 == r
+        rec1 = a.drain()
+        blob = a.checkpoint()
+    full = dzs.dzs_footprint_bytes(dzs.params(**KW2, precision=precision))
+    shrunk = dzs.dzs_footprint_bytes(dzs.params(**KW2, precision=precision, capacity=n))
+    assert shrunk < full
+    with dzs.Context(**KW2, precision=precision, capacity=n) as b:
+        with pytest.raises(dzs.DzsError):
+            b.ics()  # the ICs need all n1d^3 slots
+        b.restore(blob)
+        b.step(96)
+        st_b, rec2 = b.state(), b.drain()
+    for name in st_ref:
+        assert np.array_equal(st_b[name], st_ref[name]), name
+    assert np.concatenate([rec1, rec2]).tobytes() == rec_ref.tobytes()
+
+
+def test_wall_limit_halts(dzs):
+    with dzs.Context(**KW2) as a:
+        a.ics()
+        done, why, r = a.step_until(96, ratio_min=0.5, wall_limit_s=1e-9, horizon_s=1e9)
+        assert done == 1 and why == dzs.HALT_WALL and r == 1.0  # R flat: no re-allocation due
+        done, why, r = a.step_until(96, ratio_min=0.9)
+        assert why == dzs.HALT_RATIO
+        # while R falls, the extrapolation at the limit crosses 0.5 within the horizon
+        fell = False
+        for _ in range(10):
+            done, why, r2 = a.step_until(96, ratio_min=0.5, wall_limit_s=1e-9, horizon_s=1e9)
+            assert done == 1
+            if r2 < r:
+                fell = True
+                assert why == dzs.HALT_PREDICTED or (why == dzs.HALT_RATIO and r2 < 0.5)
+            else:
+                assert why == dzs.HALT_WALL
+            r = r2
+        assert fell
