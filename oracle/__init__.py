@@ -100,6 +100,13 @@ def _declare(L):
         "dzso_step": (i64, [P, i32, i64, vp, vp, vp, vp, vp, vp, vp, vp]),
         "dzso_diagnostics": (None, [P, i64, vp, vp, vp, vp]),
         "dzso_initial_flags": (None, [P, i64, vp, vp]),
+        "dzso_ang2pix_ring": (i64, [i64, d, d, d]),
+        "dzso_pix2ring": (None, [i64, i64, vp, vp, vp, vp]),
+        "dzso_pix2vec_ring": (None, [i64, i64, vp]),
+        "dzso_ang2pix_ring_many": (None, [i64, i64, vp, vp]),
+        "dzso_pix2vec_ring_many": (None, [i64, i64, vp, vp]),
+        "dzso_skymap": (None, [P, i64, vp, i64, d, d, vp]),
+        "dzso_pix2zphi_ring_many": (None, [i64, i64, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -335,3 +342,47 @@ def initial_state(P):
           "id": st["id"][perm].copy(), "fl": st["fl"][perm].copy()}
     st["g"] = accel(P, st["u"], st["k"])
     return st
+
+
+# ---------------- lightcone observables ----------------
+
+def ang2pix(nside, v):
+    """RING pixel of each direction v [3, n] (need not be unit vectors)"""
+    v = _c(np.atleast_2d(np.asarray(v, np.float64).T).T, np.float64)
+    if v.ndim == 1:
+        v = v.reshape(3, 1)
+    n = v.shape[1]
+    pix = np.zeros(n, np.int64)
+    lib().dzso_ang2pix_ring_many(int(nside), n, _ptr(v), _ptr(pix))
+    return pix
+
+
+def pix2vec(nside, pix):
+    pix = _c(np.atleast_1d(pix), np.int64)
+    v = np.zeros((3, len(pix)))
+    lib().dzso_pix2vec_ring_many(int(nside), len(pix), _ptr(pix), _ptr(v))
+    return v
+
+
+def pix2ring(nside, pix):
+    """-> (ring 1..4 nside - 1, position j 1-based, z, phi) of one pixel"""
+    r, j, z, ph = C.c_int64(0), C.c_int64(0), C.c_double(0), C.c_double(0)
+    lib().dzso_pix2ring(int(nside), int(pix), byref(r), byref(j), byref(z), byref(ph))
+    return r.value, j.value, z.value, ph.value
+
+
+def pix2zphi(nside, pix):
+    """centre z = cos(theta) and phi of each pixel"""
+    pix = _c(np.atleast_1d(pix), np.int64)
+    z, ph = np.zeros(len(pix)), np.zeros(len(pix))
+    lib().dzso_pix2zphi_ring_many(int(nside), len(pix), _ptr(pix), _ptr(z), _ptr(ph))
+    return z, ph
+
+
+def skymap(P, rec, nside, a_lo=0.0, a_hi=2.0):
+    """mass (sum of k) per RING pixel of the records with a_lo <= a_cross < a_hi"""
+    rec = np.ascontiguousarray(rec, RECORD_DTYPE)
+    m = np.zeros(12 * nside * nside, np.uint64)
+    lib().dzso_skymap(byref(P), len(rec), rec.ctypes.data_as(C.c_void_p), int(nside), float(a_lo),
+                      float(a_hi), _ptr(m))
+    return m

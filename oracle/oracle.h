@@ -156,4 +156,21 @@ void dzso_diagnostics(const dzso_params* P, int64_t n, const uint32_t* u,
 /* PHYSICAL mode: flag particles outside R_lc(a_init) as crossed, no record */
 void dzso_initial_flags(const dzso_params* P, int64_t n, const uint32_t* u, uint8_t* fl);
 
+/* ---- lightcone observables (observe.c) ---- */
+/* RING-ordered pixel of the direction (x, y, z) on the equal-area sphere
+ * pixelisation with 12 nside^2 pixels (Górski et al. 2005); (0,0,0) -> +z */
+int64_t dzso_ang2pix_ring(int64_t nside, double x, double y, double z);
+/* ring index (1 .. 4 nside - 1, north to south), 1-based position j in the
+ * ring, and the centre z = cos(theta), phi of a pixel; any pointer may be NULL */
+void dzso_pix2ring(int64_t nside, int64_t pix, int64_t* ring, int64_t* j, double* z, double* phi);
+void dzso_pix2vec_ring(int64_t nside, int64_t pix, double v[3]);
+/* add the mass k of every record with a_lo <= a_cross < a_hi to the pixel of
+ * its direction from the observer at the box centre (map: 12 nside^2) */
+void dzso_skymap(const dzso_params* P, int64_t nrec, const dzso_record* rec, int64_t nside, double a_lo,
+                 double a_hi, uint64_t* map);
+/* the same for n points: v [3][n] -> pix [n]; pix [n] -> centres v [3][n] */
+void dzso_ang2pix_ring_many(int64_t nside, int64_t n, const double* v, int64_t* pix);
+void dzso_pix2vec_ring_many(int64_t nside, int64_t n, const int64_t* pix, double* v);
+void dzso_pix2zphi_ring_many(int64_t nside, int64_t n, const int64_t* pix, double* z, double* phi);
+
 #endif

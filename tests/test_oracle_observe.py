@@ -1,0 +1,153 @@
+"""Pins of the oracle's lightcone observables (oracle/observe.c, oracle/sht.py).
+
+Paper Sec. 3.1.2: lightcone mass projected on an equal-area sky pixelisation
+(Górski et al. 2005, RING order) and its angular power spectrum.  Pins: the
+12 base pixels of Nside = 1 at their textbook centres; every pixel centre maps
+back to its own pixel; ring sizes and latitudes of the scheme; equal areas by
+Monte Carlo (chi^2 of uniform directions) and a bound on the distance of a
+direction to its pixel centre; known pixels of the axes; the sky map keeps
+the record mass and honours the a* window; the harmonic analysis returns the
+closed-form coefficients of a constant, a dipole and single-harmonic maps."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import sht
+
+
+def test_base_pixels_nside1():
+    z, phi = O.pix2zphi(1, np.arange(12))
+    q = np.pi / 4
+    assert np.allclose(z, [2 / 3] * 4 + [0] * 4 + [-2 / 3] * 4, atol=1e-15)
+    want = [q, 3 * q, 5 * q, 7 * q, 0, 2 * q, 4 * q, 6 * q, q, 3 * q, 5 * q, 7 * q]
+    assert np.allclose(phi, want, atol=1e-15)
+
+
+@pytest.mark.parametrize("nside", [1, 2, 4, 8, 16, 64, 256])
+def test_centres_round_trip(nside):
+    pix = np.arange(12 * nside * nside)
+    assert np.array_equal(O.ang2pix(nside, O.pix2vec(nside, pix)), pix)
+
+
+@pytest.mark.parametrize("nside", [1, 4, 32])
+def test_ring_structure(nside):
+    npix = 12 * nside * nside
+    rings = np.array([O.pix2ring(nside, p)[0] for p in range(npix)])
+    z, phi = O.pix2zphi(nside, np.arange(npix))
+    assert rings.min() == 1 and rings.max() == 4 * nside - 1
+    assert np.all(np.diff(rings) >= 0)  # RING order runs north to south
+    for i in range(1, 4 * nside):
+        sel = rings == i
+        size = 4 * min(i, nside, 4 * nside - i)
+        assert sel.sum() == size
+        zi = z[sel]
+        assert np.all(zi == zi[0])
+        if i < nside:
+            assert math.isclose(zi[0], 1 - i * i / (3 * nside * nside), rel_tol=0, abs_tol=1e-15)
+        elif i <= 3 * nside:
+            assert math.isclose(zi[0], 4 / 3 - 2 * i / (3 * nside), rel_tol=0, abs_tol=1e-15)
+        # equally spaced in phi, increasing
+        d = np.diff(phi[sel])
+        assert np.allclose(d, 2 * np.pi / size, rtol=1e-13)
+
+
+def test_axes():
+    for nside in (1, 2, 256, 1024):
+        npix = 12 * nside * nside
+        assert O.ang2pix(nside, np.array([0.0, 0.0, 1.0])) == 0
+        assert O.ang2pix(nside, np.array([0.0, 0.0, -1.0])) == npix - 4
+        eq = npix // 2 - 2 * nside  # first pixel of the equatorial ring 2 nside
+        assert O.ang2pix(nside, np.array([1.0, 0.0, 0.0])) == eq
+        assert O.ang2pix(nside, np.array([0.0, 1.0, 0.0])) == eq + nside
+        assert O.ang2pix(nside, np.array([-1.0, 0.0, 0.0])) == eq + 2 * nside
+        assert O.ang2pix(nside, np.array([0.0, 0.0, 0.0])) == 0
+
+
+@pytest.mark.parametrize("nside", [2, 4, 16])
+def test_equal_area_and_locality(nside):
+    rng = np.random.default_rng(7)
+    n = 2_000_000
+    v = rng.normal(size=(3, n))
+    pix = O.ang2pix(nside, v)
+    npix = 12 * nside * nside
+    cnt = np.bincount(pix, minlength=npix)
+    mean = n / npix
+    from scipy.stats import chi2
+    stat = ((cnt - mean) ** 2 / mean).sum()
+    p = chi2.sf(stat, npix - 1)
+    assert 1e-5 < p < 1 - 1e-5
+    assert np.abs(cnt - mean).max() < 5.5 * math.sqrt(mean)
+    # every direction lies within ~ one pixel size of its pixel centre
+    c = O.pix2vec(nside, pix[:200_000])
+    u = v[:, :200_000] / np.linalg.norm(v[:, :200_000], axis=0)
+    ang = np.arccos(np.clip((c * u).sum(axis=0), -1, 1))
+    assert ang.max() < 1.5 * math.sqrt(4 * math.pi / npix)
+
+
+def test_skymap_mass_and_window():
+    P = O.params(n1d=8, mesh=16, box=16.0)
+    rng = np.random.default_rng(3)
+    rec = np.zeros(5000, O.RECORD_DTYPE)
+    rec["k"] = rng.integers(1, 9, size=5000)
+    rec["a_cross"] = rng.uniform(0.02, 1.0, size=5000)
+    rec["x"] = rng.uniform(0, 16.0, size=(5000, 3))
+    rec["x"][0] = 8.0  # at the observer: direction +z
+    rec["a_cross"][0] = 0.5
+    m = O.skymap(P, rec, 8)
+    assert m.sum() == rec["k"].sum() and m[0] >= rec["k"][0]
+    lo, hi = 0.3, 0.7
+    mw = O.skymap(P, rec, 8, lo, hi)
+    inw = (rec["a_cross"] >= lo) & (rec["a_cross"] < hi)
+    assert mw.sum() == rec["k"][inw].sum()
+    # per record: its pixel is the one of its direction from the box centre
+    sel = np.nonzero(inw)[0][:50]
+    for r in sel:
+        one = O.skymap(P, rec[r:r + 1], 8, lo, hi)
+        assert one[O.ang2pix(8, rec["x"][r] - 8.0)] == rec["k"][r]
+
+
+NS = 8
+
+
+@pytest.fixture(scope="module")
+def angles():
+    return sht.pixel_angles(NS)
+
+
+def test_constant_map(angles):
+    c = 3.5
+    a = sht.alm(np.full(12 * NS * NS, c), NS, 12, angles)
+    assert abs(a[0, 0] - c * math.sqrt(4 * math.pi)) < 1e-12
+    assert math.isclose(sht.cl(a)[0], 4 * math.pi * c * c, rel_tol=1e-12)
+    # every ring holds 4 i pixels: its phi sum vanishes exactly unless 4 | m;
+    # m = 0 and m = 4, 8, ...: the ring quadrature (aliasing in the polar rings)
+    nz = [mm for mm in range(1, 13) if mm % 4]
+    assert np.abs(a[:, nz]).max() < 1e-12
+    assert np.abs(a[1:NS + 1, ::4]).max() < 2e-2 * c  # l <= Nside
+
+
+def test_dipole_map(angles):
+    theta, phi = angles
+    a = sht.alm(np.cos(theta), NS, 6, angles)
+    assert abs(a[1, 0] / math.sqrt(4 * math.pi / 3) - 1) < 2e-3  # quadrature: 1.5e-3 at Nside 8
+    off = np.abs(a).copy()
+    off[1, 0] = 0
+    assert off.max() < 2e-2
+
+
+@pytest.mark.parametrize("l,m", [(2, 0), (3, 1), (5, 4), (7, 2)])
+def test_single_harmonic(angles, l, m):
+    """map = Re Y_lm: a_lm = 1/2 (m > 0) or 1 (m = 0), everything else ~0
+    (pixel-centre quadrature, so to ~1e-2 at l < Nside)"""
+    from scipy.special import sph_harm_y
+    theta, phi = angles
+    y = np.real(sph_harm_y(l, m, theta, phi))
+    a = sht.alm(y, NS, 10, angles)
+    want = 1.0 if m == 0 else 0.5
+    assert abs(a[l, m] - want) < 2e-2
+    off = np.abs(a).copy()
+    off[l, m] = 0
+    assert off.max() < 2e-2
+    assert abs(sht.alm_one(y, NS, l, m, angles) - a[l, m]) < 1e-13
