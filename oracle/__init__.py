@@ -107,6 +107,7 @@ def _declare(L):
         "dzso_pix2vec_ring_many": (None, [i64, i64, vp, vp]),
         "dzso_skymap": (None, [P, i64, vp, i64, d, d, vp]),
         "dzso_pix2zphi_ring_many": (None, [i64, i64, vp, vp, vp]),
+        "dzso_lcdensity": (None, [P, i64, vp, i64, d, d, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -386,3 +387,12 @@ def skymap(P, rec, nside, a_lo=0.0, a_hi=2.0):
     lib().dzso_skymap(byref(P), len(rec), rec.ctypes.data_as(C.c_void_p), int(nside), float(a_lo),
                       float(a_hi), _ptr(m))
     return m
+
+
+def lcdensity(P, rec, mesh, a_lo=0.0, a_hi=2.0):
+    """NGP mass grid [mesh, mesh, mesh] of the records' crossing positions"""
+    rec = np.ascontiguousarray(rec, RECORD_DTYPE)
+    g = np.zeros(mesh ** 3, np.uint64)
+    lib().dzso_lcdensity(byref(P), len(rec), rec.ctypes.data_as(C.c_void_p), int(mesh), float(a_lo),
+                         float(a_hi), _ptr(g))
+    return g.reshape(mesh, mesh, mesh)

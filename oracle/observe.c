@@ -19,6 +19,11 @@
  * |z|)) Nside = integer and (1 - t') sqrt(3 (1 - |z|)) Nside = integer
  * (t' = t - floor(t)).
  *
+ * 3D lightcone density (Sec. 3.1.3, Fig. 5: the particle lightcone written
+ * on the fly in a thin shell at R_lc): the mass k of each record in the a*
+ * window is added to the cell floor(x* / L * M) of an M^3 mesh (nearest grid
+ * point, cell [i][j][l] at index (i M + j) M + l).
+ *
  * Sky map reading: a lightcone record (Sec. 1 footnote; crossing position x*)
  * is seen in the direction x* - x_obs (x* lies in [0, L), the observer at
  * L/2, so that difference is the minimum image); its mass k is added to the
@@ -142,4 +147,18 @@ void dzso_pix2vec_ring_many(int64_t nside, int64_t n, const int64_t* pix, double
 
 void dzso_pix2zphi_ring_many(int64_t nside, int64_t n, const int64_t* pix, double* z, double* phi) {
   for (int64_t i = 0; i < n; ++i) dzso_pix2ring(nside, pix[i], NULL, NULL, &z[i], &phi[i]);
+}
+
+void dzso_lcdensity(const dzso_params* P, int64_t nrec, const dzso_record* rec, int64_t mesh, double a_lo,
+                    double a_hi, uint64_t* grid) {
+  for (int64_t r = 0; r < nrec; ++r) {
+    if (!(rec[r].a_cross >= a_lo && rec[r].a_cross < a_hi)) continue;
+    int64_t c[3];
+    for (int ax = 0; ax < 3; ++ax) {
+      c[ax] = (int64_t)floor(rec[r].x[ax] / P->box * (double)mesh);
+      if (c[ax] < 0) c[ax] = 0;
+      if (c[ax] >= mesh) c[ax] = mesh - 1;
+    }
+    grid[(c[0] * mesh + c[1]) * mesh + c[2]] += rec[r].k;
+  }
 }

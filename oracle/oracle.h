@@ -171,6 +171,10 @@ void dzso_skymap(const dzso_params* P, int64_t nrec, const dzso_record* rec, int
 /* the same for n points: v [3][n] -> pix [n]; pix [n] -> centres v [3][n] */
 void dzso_ang2pix_ring_many(int64_t nside, int64_t n, const double* v, int64_t* pix);
 void dzso_pix2vec_ring_many(int64_t nside, int64_t n, const int64_t* pix, double* v);
+/* NGP mass of the records with a_lo <= a_cross < a_hi on a mesh^3 grid of the
+ * box ([i][j][l], x* / L * mesh floored, clamped to the last cell) */
+void dzso_lcdensity(const dzso_params* P, int64_t nrec, const dzso_record* rec, int64_t mesh, double a_lo,
+                    double a_hi, uint64_t* grid);
 void dzso_pix2zphi_ring_many(int64_t nside, int64_t n, const int64_t* pix, double* z, double* phi);
 
 #endif

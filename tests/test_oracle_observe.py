@@ -108,6 +108,28 @@ def test_skymap_mass_and_window():
         assert one[O.ang2pix(8, rec["x"][r] - 8.0)] == rec["k"][r]
 
 
+def test_lcdensity_cells():
+    P = O.params(n1d=8, mesh=16, box=16.0)
+    rng = np.random.default_rng(4)
+    rec = np.zeros(3000, O.RECORD_DTYPE)
+    rec["k"] = rng.integers(1, 9, size=3000)
+    rec["a_cross"] = rng.uniform(0.02, 1.0, size=3000)
+    rec["x"] = rng.uniform(0, 16.0, size=(3000, 3))
+    rec["x"][0] = [0.0, 15.999999999, 8.0]
+    g = O.lcdensity(P, rec, 32)
+    assert g.sum() == rec["k"].sum()
+    assert g[0, 31, 16] >= rec["k"][0]
+    # brute force: cell of each record by exact comparison with the cell edges
+    want = np.zeros((32, 32, 32), np.uint64)
+    for r in rec:
+        c = [int(np.searchsorted(np.arange(1, 32) * 0.5, x, side="right")) for x in r["x"]]
+        want[tuple(c)] += r["k"]
+    assert np.array_equal(g, want)
+    lo, hi = 0.25, 0.5
+    inw = (rec["a_cross"] >= lo) & (rec["a_cross"] < hi)
+    assert O.lcdensity(P, rec, 32, lo, hi).sum() == rec["k"][inw].sum()
+
+
 NS = 8
 
 
