@@ -238,6 +238,40 @@ enum {
 DZS_API dzs_status dzs_step_until(dzs_ctx* c, int32_t max_steps, const dzs_halt* h, int32_t* steps_done,
                                   int32_t* reason, double* ratio);
 
+/* Lightcone observables (Sec. 3.1.2, Fig. 4: the lightcone mass projected on
+ * an equal-area sky map and its angular power spectrum; Sec. 3.1.3, Fig. 5:
+ * the 3D lightcone).  Once enabled, every lightcone record with
+ * a_lo <= a_cross < a_hi adds its mass k (in units of m0) to
+ *   - the pixel of its direction from the observer on the RING-ordered
+ *     equal-area pixelisation of Górski et al. (2005), 12 nside^2 pixels
+ *     (pixel index decided in FP64), and
+ *   - the NGP cell floor(x* / L * mesh) per axis of a mesh^3 grid of the box
+ *     ([i][j][l], l fastest),
+ * as the step writes the record (also when the ring is full).  Counts are
+ * exact uint64 sums.  Not part of a checkpoint. */
+typedef struct {
+  int32_t nside;  /* power of two, 1 .. 4096; 0: no sky map */
+  int32_t mesh;   /* 1 .. 1024; 0: no 3D lightcone grid */
+  double a_lo, a_hi;
+} dzs_observe;
+
+/* (Re)allocate and zero the observables; o == NULL or both sizes 0 turns them
+ * off and frees them.  DZS_EINVAL for a bad size or a_lo > a_hi. */
+DZS_API dzs_status dzs_observe_enable(dzs_ctx* c, const dzs_observe* o);
+/* Bin n caller-owned host records (e.g. drained from another run) the same way. */
+DZS_API dzs_status dzs_observe_add_records(dzs_ctx* c, const dzs_lc_record* rec, size_t n);
+/* Copy the sky map (npix = 12 nside^2) / the 3D grid (ncell = mesh^3) to host
+ * memory; DZS_EINVAL if the size differs or the observable is off. */
+DZS_API dzs_status dzs_skymap_get(dzs_ctx* c, uint64_t* map, size_t npix);
+DZS_API dzs_status dzs_lcdensity_get(dzs_ctx* c, uint64_t* grid, size_t ncell);
+/* Harmonic analysis of the sky map (values = mass per pixel):
+ * a_lm = (4 pi / npix) sum_p map_p conj(Y_lm(theta_p, phi_p)) at the pixel
+ * centres, Y_lm orthonormal with the Condon-Shortley phase, 0 <= m <= l <=
+ * lmax (lmax <= 4 nside); cl[lmax + 1] gets C_l = (|a_l0|^2 + 2 sum_m>0
+ * |a_lm|^2) / (2l + 1); alm (may be NULL) gets (re, im) pairs at index
+ * m (2 lmax + 1 - m) / 2 + l.  FP64, deterministic.  Synchronises. */
+DZS_API dzs_status dzs_skymap_alm(dzs_ctx* c, int32_t lmax, double* cl, double* alm);
+
 DZS_API dzs_status dzs_get_tables(dzs_ctx* c, double* a, double* drift, double* kick1, double* kick2,
                           double* rlc, uint64_t* rlat);
 

@@ -34,7 +34,8 @@ EXPORTED = ["dzs_params_default", "dzs_footprint_bytes", "dzs_create", "dzs_ics"
             "dzs_set_state", "dzs_accel", "dzs_merge_only", "dzs_diagnostics", "dzs_get_tables",
             "dzs_get_mesh", "dzs_get_counters", "dzs_set_profiling", "dzs_get_profile",
             "dzs_morton_sort_noalloc", "dzs_checkpoint_bytes", "dzs_checkpoint", "dzs_restore",
-            "dzs_step_until", "dzs_last_error"]
+            "dzs_step_until", "dzs_observe_enable", "dzs_observe_add_records", "dzs_skymap_get",
+            "dzs_lcdensity_get", "dzs_skymap_alm", "dzs_last_error"]
 NOALLOC_SORT_MAX_N = 262144
 PROF_NAMES = ["kick_drift", "sort", "merge", "tree", "pm", "walk"]
 
@@ -59,6 +60,10 @@ class Halt(C.Structure):
 
 
 HALT_NONE, HALT_RATIO, HALT_PREDICTED, HALT_WALL = 0, 1, 2, 3
+
+
+class Observe(C.Structure):
+    _fields_ = [("nside", C.c_int32), ("mesh", C.c_int32), ("a_lo", C.c_double), ("a_hi", C.c_double)]
 
 
 RECORD_DTYPE = np.dtype([("id", "<u4"), ("k", "<u4"), ("a_cross", "<f8"),
@@ -98,6 +103,9 @@ def load(path: str = LIB_PATH):
         "dzs_checkpoint_bytes": [vp, C.POINTER(sz)], "dzs_checkpoint": [vp, vp, sz, C.POINTER(sz)],
         "dzs_restore": [vp, vp, sz],
         "dzs_step_until": [vp, i32, C.POINTER(Halt), C.POINTER(i32), C.POINTER(i32), C.POINTER(C.c_double)],
+        "dzs_observe_enable": [vp, C.POINTER(Observe)], "dzs_observe_add_records": [vp, vp, sz],
+        "dzs_skymap_get": [vp, vp, sz], "dzs_lcdensity_get": [vp, vp, sz],
+        "dzs_skymap_alm": [vp, i32, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -268,6 +276,41 @@ def dzs_restore(h, blob: bytes):
     _check(load().dzs_restore(h, _ptr(buf), len(buf)), h)
 
 
+def dzs_observe_enable(h, nside=0, mesh=0, a_lo=0.0, a_hi=2.0):
+    o = Observe(nside, mesh, a_lo, a_hi)
+    _check(load().dzs_observe_enable(h, C.byref(o)), h)
+
+
+def dzs_observe_add_records(h, rec):
+    rec = np.ascontiguousarray(rec, RECORD_DTYPE)
+    _check(load().dzs_observe_add_records(h, rec.ctypes.data_as(C.c_void_p), len(rec)), h)
+
+
+def dzs_skymap_get(h, nside):
+    m = np.zeros(12 * nside * nside, np.uint64)
+    _check(load().dzs_skymap_get(h, _ptr(m), m.size), h)
+    return m
+
+
+def dzs_lcdensity_get(h, mesh):
+    g = np.zeros(mesh ** 3, np.uint64)
+    _check(load().dzs_lcdensity_get(h, _ptr(g), g.size), h)
+    return g.reshape(mesh, mesh, mesh)
+
+
+def dzs_skymap_alm(h, lmax):
+    """-> (C_l [lmax + 1], a_lm [lmax + 1, lmax + 1] complex indexed [l, m])"""
+    cl = np.zeros(lmax + 1)
+    raw = np.zeros(2 * (lmax + 1) * (lmax + 2) // 2)
+    _check(load().dzs_skymap_alm(h, lmax, _ptr(cl), _ptr(raw)), h)
+    a = np.zeros((lmax + 1, lmax + 1), np.complex128)
+    z = raw[0::2] + 1j * raw[1::2]
+    for m in range(lmax + 1):
+        i0 = m * (2 * lmax + 1 - m) // 2
+        a[m:, m] = z[i0 + m:i0 + lmax + 1]
+    return cl, a
+
+
 def dzs_step_until(h, max_steps: int, ratio_min=0.0, wall_limit_s=0.0, horizon_s=0.0):
     """-> (steps done, DZS_HALT_* reason, last N / N0)"""
     hp = Halt(ratio_min, wall_limit_s, horizon_s)
@@ -318,3 +361,8 @@ class Context:
     def checkpoint(self): return dzs_checkpoint(self.h)
     def restore(self, blob): dzs_restore(self.h, blob)
     def step_until(self, max_steps, **halt): return dzs_step_until(self.h, max_steps, **halt)
+    def observe(self, **kw): dzs_observe_enable(self.h, **kw)
+    def observe_add_records(self, rec): dzs_observe_add_records(self.h, rec)
+    def skymap(self, nside): return dzs_skymap_get(self.h, nside)
+    def lcdensity(self, mesh): return dzs_lcdensity_get(self.h, mesh)
+    def skymap_alm(self, lmax): return dzs_skymap_alm(self.h, lmax)

@@ -418,6 +418,9 @@ dzs_status dzs_destroy(dzs_ctx* c) {
   }
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   if (c->arena) cudaFree(c->arena);
+  if (c->obs.sky) cudaFree(c->obs.sky);
+  if (c->obs.grid) cudaFree(c->obs.grid);
+  if (c->sht_work) cudaFree(c->sht_work);
   delete c;
   return DZS_OK;
 }
@@ -825,6 +828,110 @@ dzs_status dzs_restore(dzs_ctx* c, const void* host_buf, size_t len) {
   c->g_aligned = true;
   c->amin2_ready = false;
   return DZS_OK;
+}
+
+// ---- lightcone observables
+dzs_status dzs_observe_enable(dzs_ctx* c, const dzs_observe* o) {
+  dzs_status s = guard(c);
+  if (s) return s;
+  const bool off = !o || (o->nside == 0 && o->mesh == 0);
+  if (!off) {
+    const bool pow2 = o->nside > 0 && (o->nside & (o->nside - 1)) == 0;
+    if (o->nside < 0 || (o->nside != 0 && (!pow2 || o->nside > 4096)) || o->mesh < 0 || o->mesh > 1024 ||
+        !(o->a_lo <= o->a_hi))
+      return fail(c, DZS_EINVAL, "bad observables (nside a power of two <= 4096, mesh <= 1024, a_lo <= a_hi)");
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  if (c->obs.sky) CK(cudaFree(c->obs.sky));
+  if (c->obs.grid) CK(cudaFree(c->obs.grid));
+  c->obs = dzs::ObserveTarget();
+  if (off) return DZS_OK;
+  dzs::ObserveTarget t;
+  t.nside = o->nside;
+  t.mesh = o->mesh;
+  t.a_lo = o->a_lo;
+  t.a_hi = o->a_hi;
+  t.half = 0.5 * c->P.box;
+  t.box = c->P.box;
+  if (t.nside) {
+    const size_t b = 8 * (size_t)(12 * t.nside * t.nside);
+    if (cudaMalloc((void**)&t.sky, b) != cudaSuccess) return fail(c, DZS_ENOMEM, "sky map");
+    CK(cudaMemset(t.sky, 0, b));
+  }
+  if (t.mesh) {
+    const size_t b = 8 * (size_t)t.mesh * t.mesh * t.mesh;
+    if (cudaMalloc((void**)&t.grid, b) != cudaSuccess) {
+      if (t.sky) cudaFree(t.sky);
+      return fail(c, DZS_ENOMEM, "3D lightcone grid");
+    }
+    CK(cudaMemset(t.grid, 0, b));
+  }
+  c->obs = t;
+  return DZS_OK;
+}
+
+dzs_status dzs_observe_add_records(dzs_ctx* c, const dzs_lc_record* rec, size_t n) {
+  dzs_status s = guard(c);
+  if (s) return s;
+  if (n && !rec) return fail(c, DZS_EINVAL, "rec is NULL");
+  if (!c->obs.sky && !c->obs.grid) return fail(c, DZS_ESTATE, "observables are off");
+  // staged through the conversion scratch (24 cap bytes), in chunks
+  const size_t chunk = (size_t)(24 * c->cap) / sizeof(dzs_lc_record);
+  dzs_lc_record* d = (dzs_lc_record*)c->B.convert;
+  for (size_t done = 0; done < n;) {
+    const size_t m = n - done < chunk ? n - done : chunk;
+    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaMemcpy(d, rec + done, m * sizeof(dzs_lc_record), cudaMemcpyHostToDevice));
+    launch_observe_records(c, d, (int64_t)m);
+    done += m;
+  }
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c->stream));
+  return check_device_errors(c);
+}
+
+dzs_status dzs_skymap_get(dzs_ctx* c, uint64_t* map, size_t npix) {
+  dzs_status s = guard(c);
+  if (s) return s;
+  if (!c->obs.sky || !map || npix != (size_t)(12 * c->obs.nside * c->obs.nside))
+    return fail(c, DZS_EINVAL, "sky map off or npix != 12 nside^2");
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaMemcpy(map, c->obs.sky, 8 * npix, cudaMemcpyDeviceToHost));
+  return DZS_OK;
+}
+
+dzs_status dzs_lcdensity_get(dzs_ctx* c, uint64_t* grid, size_t ncell) {
+  dzs_status s = guard(c);
+  if (s) return s;
+  if (!c->obs.grid || !grid || ncell != (size_t)(c->obs.mesh * c->obs.mesh * c->obs.mesh))
+    return fail(c, DZS_EINVAL, "3D lightcone grid off or ncell != mesh^3");
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaMemcpy(grid, c->obs.grid, 8 * ncell, cudaMemcpyDeviceToHost));
+  return DZS_OK;
+}
+
+dzs_status dzs_skymap_alm(dzs_ctx* c, int32_t lmax, double* cl, double* alm) {
+  dzs_status s = guard(c);
+  if (s) return s;
+  if (!c->obs.sky) return fail(c, DZS_ESTATE, "sky map off");
+  if (lmax < 0 || lmax > 4 * c->obs.nside || !cl) return fail(c, DZS_EINVAL, "need 0 <= lmax <= 4 nside, cl");
+  const size_t need = sht_work_bytes(c->obs.nside, lmax);
+  CK(cudaStreamSynchronize(c->stream));
+  if (c->sht_bytes < need) {
+    if (c->sht_work) CK(cudaFree(c->sht_work));
+    c->sht_work = nullptr;
+    c->sht_bytes = 0;
+    if (cudaMalloc(&c->sht_work, need) != cudaSuccess) return fail(c, DZS_ENOMEM, "harmonic-analysis scratch");
+    c->sht_bytes = need;
+  }
+  double2* d_alm = nullptr;
+  double* d_cl = nullptr;
+  launch_sht(c, lmax, c->sht_work, &d_alm, &d_cl);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaMemcpy(cl, d_cl, 8 * ((size_t)lmax + 1), cudaMemcpyDeviceToHost));
+  if (alm) CK(cudaMemcpy(alm, d_alm, 16 * ((size_t)lmax + 1) * (lmax + 2) / 2, cudaMemcpyDeviceToHost));
+  return check_device_errors(c);
 }
 
 dzs_status dzs_get_tables(dzs_ctx* c, double* a, double* drift, double* kick1, double* kick2, double* rlc,

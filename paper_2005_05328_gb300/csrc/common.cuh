@@ -133,6 +133,15 @@ struct Buffers {
   void* convert = nullptr;       // double [3][cap] conversion scratch
 };
 
+// where lightcone records are binned (sky map, 3D lightcone); null: nowhere
+struct ObserveTarget {
+  unsigned long long* sky = nullptr;   // [12 nside^2] mass per RING pixel, or null
+  unsigned long long* grid = nullptr;  // [mesh^3] NGP mass of crossing positions, or null
+  int64_t nside = 0, mesh = 0;
+  double a_lo = 0, a_hi = 0;           // records with a_lo <= a* < a_hi
+  double half = 0, box = 0;            // observer at (L/2, L/2, L/2)
+};
+
 }  // namespace dzs
 
 struct dzs_ctx {
@@ -164,6 +173,9 @@ struct dzs_ctx {
   char* arena = nullptr;
   size_t arena_bytes = 0;
   dzs::Buffers B;
+  dzs::ObserveTarget obs;  // device buffers owned by the context (dzs_observe_enable)
+  void* sht_work = nullptr;  // harmonic-analysis scratch (dzs_skymap_alm)
+  size_t sht_bytes = 0;
   std::string err;
   uint64_t launches = 0;  // kernels launched (host-side count)
   // per-stage CUDA-event profiling
@@ -201,6 +213,10 @@ void launch_ics(dzs_ctx* c);
 void launch_to_double(dzs_ctx* c, const void* src, int64_t count, double* dst);
 void launch_from_double(dzs_ctx* c, const double* src, int64_t count, void* dst);
 void launch_fft_init(dzs_ctx* c);
+void launch_observe_records(dzs_ctx* c, const dzs_lc_record* d_rec, int64_t n);
+size_t sht_work_bytes(int64_t nside, int lmax);
+size_t sht_shared_bytes(int lmax);
+void launch_sht(dzs_ctx* c, int lmax, void* work, double2** d_alm, double** d_cl);
 void upload_fft_constants(int dev);  // register-FFT twiddles, once per device
 template <class R>
 void fft_r2c_3d(dzs_ctx* c, const R* in, cplx<R>* out, int n, const cplx<R>* tw);

@@ -7,6 +7,7 @@
 // A particle not yet flagged is recorded when d_n < R_lc(a_n) and
 // d_n+1 >= R_lc(a_n+1), decided exactly on the integer lattice.
 #include "common.cuh"
+#include "observe.cuh"
 
 namespace dzs {
 namespace {
@@ -53,16 +54,15 @@ __global__ void k_records(const int32_t* __restrict__ d_n, int64_t cap, const ui
                           const int32_t* __restrict__ rank, dzs_lc_record* __restrict__ ring,
                           uint64_t ring_cap, uint64_t* __restrict__ counters, uint64_t drained,
                           uint32_t* __restrict__ err, double dlat, double scale, double box,
-                          double a0, double a1, double rlc0, double rlc1) {
+                          double a0, double a1, double rlc0, double rlc1, ObserveTarget obs) {
   const int64_t n = *d_n;
   const uint64_t head = counters[0];
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     if (!(fl[i] & kFlNow)) continue;
     uint64_t slot = head + (uint64_t)rank[i];
-    if (slot - drained >= ring_cap) {
-      atomicOr(err, kErrRing);
-      continue;
-    }
+    const bool room = slot - drained < ring_cap;
+    if (!room) atomicOr(err, kErrRing);
+    if (!room && !obs.sky && !obs.grid) continue;
     uint32_t ua[3], ub[3];
     double pd[3];
     for (int ax = 0; ax < 3; ++ax) {
@@ -87,7 +87,8 @@ __global__ void k_records(const int32_t* __restrict__ d_n, int64_t cap, const ui
       r.x[ax] = x;
       r.p[ax] = pd[ax];
     }
-    ring[slot % ring_cap] = r;
+    observe_record(obs, r.k, r.a_cross, r.x);  // sky map / 3D lightcone, also for a dropped record
+    if (room) ring[slot % ring_cap] = r;
   }
 }
 
@@ -185,12 +186,12 @@ void launch_records(dzs_ctx* c, int step) {
     k_records<double><<<grid, kThreads, 0, c->stream>>>(
         c->B.n, c->cap, c->B.u, (const double*)c->B.p, c->B.k, c->B.id, c->B.fl, rank, c->B.ring,
         c->ring_cap, c->B.counters, c->drained, c->B.err, dlat, c->scale, c->P.box, c->T.a[step],
-        c->T.a[step + 1], c->T.rlc[step], c->T.rlc[step + 1]);
+        c->T.a[step + 1], c->T.rlc[step], c->T.rlc[step + 1], c->obs);
   else
     k_records<float><<<grid, kThreads, 0, c->stream>>>(
         c->B.n, c->cap, c->B.u, (const float*)c->B.p, c->B.k, c->B.id, c->B.fl, rank, c->B.ring,
         c->ring_cap, c->B.counters, c->drained, c->B.err, dlat, c->scale, c->P.box, c->T.a[step],
-        c->T.a[step + 1], c->T.rlc[step], c->T.rlc[step + 1]);
+        c->T.a[step + 1], c->T.rlc[step], c->T.rlc[step + 1], c->obs);
   k_records_advance<<<1, 1, 0, c->stream>>>(c->B.n, rank, c->B.counters, c->ring_cap, c->drained);
 }
 

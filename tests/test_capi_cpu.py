@@ -88,6 +88,9 @@ def test_struct_layouts_match_the_header(tmp_path, dzs):
     body += ['  printf("%%zu\\n", offsetof(dzs_params, %s));' % f for f in fields]
     body += ['  printf("%zu\\n", sizeof(dzs_halt));']
     body += ['  printf("%%zu\\n", offsetof(dzs_halt, %s));' % f for f in halt]
+    obs = [f[0] for f in dzs.Observe._fields_]
+    body += ['  printf("%zu\\n", sizeof(dzs_observe));']
+    body += ['  printf("%%zu\\n", offsetof(dzs_observe, %s));' % f for f in obs]
     body += ['  printf("%zu\\n", sizeof(dzs_lc_record));', "  return 0;", "}"]
     src = tmp_path / "layout.c"
     src.write_text("\n".join(body) + "\n")
@@ -96,5 +99,6 @@ def test_struct_layouts_match_the_header(tmp_path, dzs):
     got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
     want = [ctypes.sizeof(dzs.Params)] + [getattr(dzs.Params, f).offset for f in fields]
     want += [ctypes.sizeof(dzs.Halt)] + [getattr(dzs.Halt, f).offset for f in halt]
+    want += [ctypes.sizeof(dzs.Observe)] + [getattr(dzs.Observe, f).offset for f in obs]
     want += [dzs.RECORD_DTYPE.itemsize]
     assert got == want

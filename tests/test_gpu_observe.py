@@ -1,0 +1,187 @@
+"""GPU parity of the lightcone observables (Sec. 3.1.2: equal-area sky map and
+its angular power spectrum; Sec. 3.1.3: 3D lightcone) against the oracle.
+
+Tolerances: pixel and cell assignments and the binned masses are integer
+work decided in FP64 on both sides, compared bit-exactly; the harmonic
+coefficients are FP64 sums in different orders (ring transform + Legendre
+recursion vs the plain per-pixel definition): |da_lm| <= 1e-10 Omega sum(map)
+(the scale of |a_lm|), C_l relative 1e-9 where C_l is not a cancellation
+residue."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import sht
+
+pytestmark = pytest.mark.gpu
+
+TWO32 = 2 ** 32
+SMALL = dict(n1d=16, mesh=32, box=32.0, merge_level=2)
+
+
+@pytest.fixture(scope="module")
+def dzs():
+    from paper_2005_05328_gb300 import build
+    build.build()
+    import paper_2005_05328_gb300 as m
+    m.load()
+    return m
+
+
+def random_records(rng, n, box, a=(0.02, 1.0)):
+    rec = np.zeros(n, O.RECORD_DTYPE)
+    rec["id"] = np.arange(n)
+    rec["k"] = rng.integers(1, 9, size=n)
+    rec["a_cross"] = rng.uniform(*a, size=n)
+    rec["x"] = rng.uniform(0, box, size=(n, 3))
+    return rec
+
+
+def edge_records(box):
+    """the observer itself, the axes, cap/belt boundary directions, box edges"""
+    h = box / 2
+    xs = [(h, h, h), (h + 1, h, h), (h - 1, h, h), (h, h + 1, h), (h, h - 1, h), (h, h, h + 1), (h, h, h - 1),
+          (h + math.sqrt(5) / 3 * 3, h, h + 2.0), (h, h + math.sqrt(5), h - 2.0), (0.0, 0.0, 0.0),
+          (box * (1 - 1e-15), box * (1 - 1e-15), 0.0), (h + 1, h + 1, h + 1), (h - 1, h - 1, h - 1)]
+    rec = np.zeros(len(xs), O.RECORD_DTYPE)
+    rec["k"] = np.arange(1, len(xs) + 1)
+    rec["a_cross"] = 0.5
+    rec["x"] = np.array(xs)
+    return rec
+
+
+@pytest.mark.parametrize("nside,mesh", [(1, 1), (8, 16), (64, 32), (1024, 64)])
+def test_binning_bit_exact(dzs, nside, mesh):
+    rng = np.random.default_rng(nside)
+    P = O.params(**SMALL)
+    rec = np.concatenate([random_records(rng, 200_000, P.box), edge_records(P.box)])
+    lo, hi = 0.3, 0.8
+    rec["a_cross"][:3] = [lo, hi, np.nextafter(hi, 0)]  # window edges: in, out, in
+    with dzs.Context(**SMALL) as ctx:
+        ctx.observe(nside=nside, mesh=mesh, a_lo=lo, a_hi=hi)
+        ctx.observe_add_records(rec[:1000])
+        ctx.observe_add_records(rec[1000:])
+        sky = ctx.skymap(nside)
+        grid = ctx.lcdensity(mesh)
+    assert np.array_equal(sky, O.skymap(P, rec, nside, lo, hi))
+    assert np.array_equal(grid, O.lcdensity(P, rec, mesh, lo, hi))
+    inw = (rec["a_cross"] >= lo) & (rec["a_cross"] < hi)
+    assert sky.sum() == rec["k"][inw].sum()
+
+
+def test_step_records_binned_as_made(dzs):
+    """the record kernel bins each record as it writes it: the fused map of a
+    run equals the map of its drained records; one injected step equals the
+    oracle's map of its own records"""
+    nside, mesh = 32, 16
+    with dzs.Context(**SMALL, precision=0) as ctx:
+        ctx.observe(nside=nside, mesh=mesh, a_lo=0.0, a_hi=2.0)
+        ctx.ics()
+        ctx.step(200)
+        rec = ctx.drain()
+        fused, fgrid = ctx.skymap(nside), ctx.lcdensity(mesh)
+    assert fused.sum() == rec["k"].sum() == 16 ** 3  # every particle crossed once by a = 1
+    with dzs.Context(**SMALL) as c2:
+        c2.observe(nside=nside, mesh=mesh, a_lo=0.0, a_hi=2.0)
+        c2.observe_add_records(rec)
+        assert np.array_equal(c2.skymap(nside), fused)
+        assert np.array_equal(c2.lcdensity(mesh), fgrid)
+    # one step from an injected oracle state, against the oracle's own records
+    P = O.params(**SMALL)
+    st = O.initial_state(P)
+    for n in range(60):
+        st, _ = O.step(P, n, st)
+    so, orec = O.kick_drift_cross(P, 60, st, st["g"])
+    assert len(orec) > 10
+    with dzs.Context(**SMALL, precision=1) as ctx:
+        ctx.observe(nside=nside, mesh=mesh, a_lo=0.0, a_hi=2.0)
+        ctx.set_state(st, 60)
+        ctx.run_stages(dzs.STAGE_KICK_DRIFT)
+        assert np.array_equal(ctx.skymap(nside), O.skymap(P, orec, nside))
+        assert np.array_equal(ctx.lcdensity(mesh), O.lcdensity(P, orec, mesh))
+
+
+def centre_records(nside, masses, box):
+    """one record per pixel, at its centre direction, carrying that pixel's mass"""
+    v = O.pix2vec(nside, np.arange(12 * nside * nside))
+    rec = np.zeros(v.shape[1], O.RECORD_DTYPE)
+    rec["k"] = masses
+    rec["a_cross"] = 0.5
+    rec["x"] = (box / 2 + 0.25 * box * v).T
+    return rec
+
+
+@pytest.mark.parametrize("nside,lmax", [(1, 2), (8, 23), (16, 40)])
+def test_alm_matches_definition(dzs, nside, lmax):
+    rng = np.random.default_rng(100 + nside)
+    P = O.params(**SMALL)
+    npix = 12 * nside * nside
+    rec = centre_records(nside, rng.integers(0, 1000, size=npix), P.box)
+    with dzs.Context(**SMALL) as ctx:
+        ctx.observe(nside=nside)
+        ctx.observe_add_records(rec)
+        m = ctx.skymap(nside)
+        cl, a = ctx.skymap_alm(lmax)
+    om = O.skymap(P, rec, nside)
+    assert np.array_equal(m, om) and np.array_equal(om, rec["k"])
+    want = sht.alm(om.astype(np.float64), nside, lmax)
+    scale = 4 * math.pi / npix * om.sum()
+    assert np.abs(a - want).max() <= 1e-10 * scale
+    wcl = sht.cl(want)
+    assert np.allclose(cl, wcl, rtol=1e-9, atol=1e-18 * scale ** 2)
+
+
+def test_alm_full_size_sampled(dzs):
+    """Nside 256, lmax 767 (the paper's map size) on a map of 2M records;
+    sampled coefficients against the definition: live below l = 600, from
+    tests/golden/alm_nside256_seed5.json (written by make_alm_golden.py from
+    the oracle) above it"""
+    import hashlib
+    import json
+    import os
+    from observe_inputs import random_records as seeded_records
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "alm_nside256_seed5.json")))
+    nside, lmax = 256, 767
+    P = O.params(**SMALL)
+    rec = seeded_records(gold["seed"], gold["n_records"], gold["box"])
+    with dzs.Context(**SMALL) as ctx:
+        ctx.observe(nside=nside)
+        ctx.observe_add_records(rec)
+        sky = ctx.skymap(nside)
+        cl, a = ctx.skymap_alm(lmax)
+    m = O.skymap(P, rec, nside)
+    assert np.array_equal(sky, m)
+    assert hashlib.sha256(m.tobytes()).hexdigest() == gold["map_sha256"], "seeded records differ from the golden's"
+    om = m.astype(np.float64)
+    ang = sht.pixel_angles(nside)
+    scale = 4 * math.pi / om.size * om.sum()
+    for l, mm in [(0, 0), (1, 0), (1, 1), (2, 1), (17, 0), (64, 63), (300, 7), (500, 499), (599, 300),
+                  (512, 256)]:
+        w = sht.alm_one(om, nside, l, mm, ang)
+        assert abs(a[l, mm] - w) <= 1e-10 * scale, (l, mm, a[l, mm], w)
+    for l, mm, re, im in gold["alm"]:
+        assert abs(a[l, mm] - complex(re, im)) <= 1e-10 * scale, (l, mm, a[l, mm], re, im)
+    # C_0 of the monopole is exact up to rounding
+    assert math.isclose(cl[0], abs(a[0, 0]) ** 2, rel_tol=1e-15)
+    assert math.isclose(a[0, 0].real, om.sum() * math.sqrt(4 * math.pi) / om.size, rel_tol=1e-12)
+
+
+def test_observe_errors(dzs):
+    with dzs.Context(**SMALL) as ctx:
+        with pytest.raises(dzs.DzsError) as e:
+            ctx.skymap_alm(4)
+        assert e.value.status == dzs.DZS_ESTATE
+        for bad in (dict(nside=3), dict(nside=8192), dict(mesh=2000), dict(nside=4, a_lo=1.0, a_hi=0.5)):
+            with pytest.raises(dzs.DzsError) as e:
+                ctx.observe(**bad)
+            assert e.value.status == dzs.DZS_EINVAL
+        ctx.observe(nside=4)
+        with pytest.raises(dzs.DzsError):
+            ctx.skymap_alm(17)  # lmax > 4 nside
+        with pytest.raises(dzs.DzsError):
+            ctx.lcdensity(8)  # grid off
+        ctx.observe()  # off
+        with pytest.raises(dzs.DzsError):
+            ctx.skymap(4)

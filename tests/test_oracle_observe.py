@@ -173,3 +173,23 @@ def test_single_harmonic(angles, l, m):
     off[l, m] = 0
     assert off.max() < 2e-2
     assert abs(sht.alm_one(y, NS, l, m, angles) - a[l, m]) < 1e-13
+
+
+def test_ylm_routes_agree():
+    """the three library routes to Y_lm agree where they overlap"""
+    mpmath = pytest.importorskip("mpmath")
+    from scipy.special import sph_harm_y
+    th = np.array([0.05, 0.7, 1.5707963267948966, 2.9])
+    ph = np.array([0.3, 1.1, 4.0, 6.0])
+    for l, m in [(3, 0), (40, 0), (40, 13), (500, 250), (599, 3)]:
+        a = sht.ylm(l, m, th, ph)
+        b = sht._ylm_mpmath(l, m, th, ph)
+        c = sph_harm_y(l, m, th, ph)
+        assert np.allclose(a, b, rtol=0, atol=1e-11)
+        assert np.allclose(c, b, rtol=0, atol=1e-11)
+    # past scipy's range: finite, and orthonormal over a fine theta grid
+    x, w = np.polynomial.legendre.leggauss(1200)
+    t = np.arccos(x)
+    y = sht.ylm(767, 383, t, np.zeros_like(t)).real
+    assert np.all(np.isfinite(y))
+    assert abs(2 * np.pi * np.sum(w * y * y) - 1) < 1e-9
