@@ -193,3 +193,76 @@ def test_ylm_routes_agree():
     y = sht.ylm(767, 383, t, np.zeros_like(t)).real
     assert np.all(np.isfinite(y))
     assert abs(2 * np.pi * np.sum(w * y * y) - 1) < 1e-9
+
+
+# ---------------------------------------------------------------- P(k)
+
+def test_pk_bins_integer_rounding():
+    from oracle import pk
+    b, n2 = pk.mode_bins(16)
+    r = np.sqrt(n2)
+    nz = n2 > 0
+    assert np.all((b[nz] - 0.5) ** 2 <= n2[nz]) and np.all(n2 < (b + 0.5) ** 2)
+    assert b[0, 0, 0] == 0 and b[1, 0, 0] == 1 and b[1, 1, 0] == 1 and b[1, 1, 1] == 2
+    assert np.all(np.abs(b - r) <= 0.5)
+
+
+@pytest.mark.parametrize("n0", [(3, 0, 0), (2, 2, 1), (0, 5, 4)])
+def test_pk_single_mode(n0):
+    """delta = A cos(2 pi n0.x / M): all power A^2 L^3 / 2 (modes +-n0) in the
+    bin round(|n0|), nothing elsewhere"""
+    from oracle import pk
+    P = O.params(n1d=8, mesh=16, box=40.0)
+    M, A = 16, 0.3
+    i = np.arange(M)
+    ph = 2 * np.pi * (n0[0] * i[:, None, None] + n0[1] * i[None, :, None] + n0[2] * i[None, None, :]) / M
+    delta = A * np.cos(ph)
+    k, p, nm = pk.pk_from_delta(P, delta, 7, deconvolve=False)
+    tot = p * nm
+    b = int(round(math.sqrt(sum(x * x for x in n0))))
+    assert math.isclose(tot[b - 1], A * A * P.box ** 3 / 2, rel_tol=1e-12)
+    assert np.abs(np.delete(tot, b - 1)).max() < 1e-12 * tot[b - 1]
+    assert np.all(nm > 0) and math.isclose(k[0], 2 * np.pi / P.box * np.mean(
+        np.sqrt(pk.mode_bins(M)[1][pk.mode_bins(M)[0] == 1])), rel_tol=1e-14)
+
+
+def test_pk_poisson_sample():
+    """uniform random unit-mass particles: the deconvolved power equals the
+    CIC shot-noise closed form P_shot C(k) / W(k)^2, C = prod (1 - 2/3 sin^2(pi
+    n_i / M)) (the sum over aliases of the CIC window, Jing 2005), so the
+    shot-subtracted P(k) is P_shot (C / W^2 - 1) within sample variance"""
+    from oracle import pk
+    rng = np.random.default_rng(11)
+    P = O.params(n1d=32, mesh=32, box=64.0)
+    n = 32 ** 3
+    u = rng.integers(0, 2 ** 32, size=(3, n), dtype=np.uint64).astype(np.uint32)
+    k = np.ones(n, np.uint32)
+    kk, pw, nm = pk.power_spectrum(P, u, k, 15)
+    shot = P.box ** 3 / n
+    M = 32
+    s = np.fft.fftfreq(M, 1.0 / M)
+    w1 = np.sinc(s / M) ** 2
+    c1 = 1 - 2.0 / 3.0 * np.sin(np.pi * s / M) ** 2
+    ratio = (c1[:, None, None] * c1[None, :, None] * c1[None, None, :]) / (
+        w1[:, None, None] * w1[None, :, None] * w1[None, None, :]) ** 2
+    b, _ = pk.mode_bins(M)
+    for j in range(1, 16):
+        want = shot * (ratio[b == j].mean() - 1)
+        sig = shot * ratio[b == j].mean() / math.sqrt(nm[j - 1] / 2)  # Hermitian pairs
+        assert abs(pw[j - 1] - want) < 5 * sig, (j, pw[j - 1], want, sig)
+
+
+def test_pk_of_initial_conditions_is_linear_theory():
+    """the ICs' particles at z = 49 follow P_lin(k) D+(a_i)^2 bin by bin.  A
+    displaced lattice carries no Poisson shot noise, so the subtracted P_shot
+    is added back here (the subtraction is meant for evolved, Poisson-like
+    particle sets)"""
+    from oracle import pk
+    P = O.params(n1d=32, mesh=64, box=256.0, seed=3)
+    st = O.ics(P)
+    k, p, nm = pk.power_spectrum(P, st["u"], st["k"], 12)
+    p = p + P.box ** 3 / 32 ** 3
+    D = O.growth(P, 1 / 50)
+    for j in range(12):
+        want = O.power(P, k[j]) * D * D
+        assert abs(p[j] / want - 1) < 5 * math.sqrt(2.0 / nm[j]), (j, p[j], want)
