@@ -272,6 +272,18 @@ DZS_API dzs_status dzs_lcdensity_get(dzs_ctx* c, uint64_t* grid, size_t ncell);
  * m (2 lmax + 1 - m) / 2 + l.  FP64, deterministic.  Synchronises. */
 DZS_API dzs_status dzs_skymap_alm(dzs_ctx* c, int32_t lmax, double* cl, double* alm);
 
+/* 3D power spectrum of the current particles (the time-slice P(k) compared
+ * between DZS and standard runs): CIC deposit of the masses on the PM mesh,
+ * delta = n / nbar - 1, forward FFT, P_mode = |delta_k|^2 L^3 / M^6 / W(k)^2
+ * - P_shot with W = prod_i sinc^2(pi n_i / M) and P_shot = L^3 sum k^2 /
+ * (sum k)^2; bin b = 1..nbins holds the modes with round(|n|) = b (|n| =
+ * |k| L / 2 pi, rounding decided on integers).  k[b] = mean |k| [h/Mpc],
+ * pk[b] = mean P_mode [(Mpc/h)^3], nmodes[b] = number of modes (k and nmodes
+ * may be NULL).  1 <= nbins <= mesh / 2.  Arithmetic in the context's
+ * precision, sums in FP64 in a fixed order.  Overwrites the meshes
+ * dzs_get_mesh returns; the state and its order are unchanged.  Synchronises. */
+DZS_API dzs_status dzs_power_spectrum(dzs_ctx* c, int32_t nbins, double* k, double* pk, double* nmodes);
+
 DZS_API dzs_status dzs_get_tables(dzs_ctx* c, double* a, double* drift, double* kick1, double* kick2,
                           double* rlc, uint64_t* rlat);
 

@@ -35,7 +35,7 @@ EXPORTED = ["dzs_params_default", "dzs_footprint_bytes", "dzs_create", "dzs_ics"
             "dzs_get_mesh", "dzs_get_counters", "dzs_set_profiling", "dzs_get_profile",
             "dzs_morton_sort_noalloc", "dzs_checkpoint_bytes", "dzs_checkpoint", "dzs_restore",
             "dzs_step_until", "dzs_observe_enable", "dzs_observe_add_records", "dzs_skymap_get",
-            "dzs_lcdensity_get", "dzs_skymap_alm", "dzs_last_error"]
+            "dzs_lcdensity_get", "dzs_skymap_alm", "dzs_power_spectrum", "dzs_last_error"]
 NOALLOC_SORT_MAX_N = 262144
 PROF_NAMES = ["kick_drift", "sort", "merge", "tree", "pm", "walk"]
 
@@ -105,7 +105,7 @@ def load(path: str = LIB_PATH):
         "dzs_step_until": [vp, i32, C.POINTER(Halt), C.POINTER(i32), C.POINTER(i32), C.POINTER(C.c_double)],
         "dzs_observe_enable": [vp, C.POINTER(Observe)], "dzs_observe_add_records": [vp, vp, sz],
         "dzs_skymap_get": [vp, vp, sz], "dzs_lcdensity_get": [vp, vp, sz],
-        "dzs_skymap_alm": [vp, i32, vp, vp],
+        "dzs_skymap_alm": [vp, i32, vp, vp], "dzs_power_spectrum": [vp, i32, vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -311,6 +311,13 @@ def dzs_skymap_alm(h, lmax):
     return cl, a
 
 
+def dzs_power_spectrum(h, nbins):
+    """-> (k [h/Mpc], P(k) [(Mpc/h)^3], modes) per bin"""
+    k, p, n = np.zeros(nbins), np.zeros(nbins), np.zeros(nbins)
+    _check(load().dzs_power_spectrum(h, nbins, _ptr(k), _ptr(p), _ptr(n)), h)
+    return k, p, n
+
+
 def dzs_step_until(h, max_steps: int, ratio_min=0.0, wall_limit_s=0.0, horizon_s=0.0):
     """-> (steps done, DZS_HALT_* reason, last N / N0)"""
     hp = Halt(ratio_min, wall_limit_s, horizon_s)
@@ -366,3 +373,4 @@ class Context:
     def skymap(self, nside): return dzs_skymap_get(self.h, nside)
     def lcdensity(self, mesh): return dzs_lcdensity_get(self.h, mesh)
     def skymap_alm(self, lmax): return dzs_skymap_alm(self.h, lmax)
+    def power_spectrum(self, nbins): return dzs_power_spectrum(self.h, nbins)

@@ -9,6 +9,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "common.cuh"
 
@@ -931,6 +932,40 @@ dzs_status dzs_skymap_alm(dzs_ctx* c, int32_t lmax, double* cl, double* alm) {
   CK(cudaStreamSynchronize(c->stream));
   CK(cudaMemcpy(cl, d_cl, 8 * ((size_t)lmax + 1), cudaMemcpyDeviceToHost));
   if (alm) CK(cudaMemcpy(alm, d_alm, 16 * ((size_t)lmax + 1) * (lmax + 2) / 2, cudaMemcpyDeviceToHost));
+  return check_device_errors(c);
+}
+
+dzs_status dzs_power_spectrum(dzs_ctx* c, int32_t nbins, double* k, double* pk, double* nmodes) {
+  dzs_status s = guard(c);
+  if (s) return s;
+  if (!c->have_state) return fail(c, DZS_ESTATE, "no particle state");
+  if (nbins < 1 || nbins > c->M / 2 || !pk) return fail(c, DZS_EINVAL, "need 1 <= nbins <= mesh / 2, pk");
+  // shot noise L^3 sum k^2 / (sum k)^2; sum k = N0 (mass is conserved exactly)
+  unsigned long long* k2 = (unsigned long long*)(c->B.counters + 15);
+  launch_sum_k2(c, k2);
+  unsigned long long sk2 = 0;
+  CK(cudaMemcpyAsync(&sk2, k2, sizeof sk2, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  const double L = c->P.box, n0 = (double)c->N0;
+  const double shot = L * L * L * (double)sk2 / (n0 * n0);
+  // CIC needs the Morton order: sort, bin, then put the state back in its order
+  // (g is not moved by either, so it stays with its particles)
+  double* part = (double*)c->B.phi;  // mesh scratch: M nbins 3 + nbins 3 doubles
+  double* out = part + (size_t)c->M * nbins * 3;
+  launch_keys(c);
+  launch_sort(c);
+  launch_pk(c, nbins, part, out, shot);
+  std::vector<double> h((size_t)nbins * 3);
+  CK(cudaMemcpyAsync(h.data(), out, 8 * h.size(), cudaMemcpyDeviceToHost, c->stream));
+  launch_unpermute(c, (double*)c->B.convert);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c->stream));
+  for (int b = 0; b < nbins; ++b) {
+    const double cnt = h[3 * b];
+    if (nmodes) nmodes[b] = cnt;
+    if (k) k[b] = cnt > 0 ? h[3 * b + 1] / cnt : 0.0;
+    pk[b] = cnt > 0 ? h[3 * b + 2] / cnt : 0.0;
+  }
   return check_device_errors(c);
 }
 

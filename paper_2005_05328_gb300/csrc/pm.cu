@@ -138,7 +138,137 @@ void pm_impl(dzs_ctx* c, bool want_pm) {
   }
 }
 
+// ---- 3D power spectrum of the mesh (forward spectrum of the CIC delta)
+//
+// P_mode = |delta_k|^2 L^3 / M^6 / W(k)^2 - P_shot, W = prod_i sinc^2(pi n_i / M),
+// bin b = round(|n|) decided on integers ((b - 1/2)^2 <= |n|^2 < (b + 1/2)^2),
+// a half-spectrum mode with 0 < kz < M/2 standing for itself and its conjugate.
+// One block per kx plane: each warp takes 32 consecutive (ky, kz) modes at a
+// time; lanes of one bin are summed in lane order by their lowest lane, which
+// adds to the warp's row of bins; the warps' rows are summed in warp order.
+// A second pass sums the planes in kx order: deterministic.
+constexpr int kPkThreads = 256;
+
+__device__ __forceinline__ int mode_bin(int64_t n2) {
+  int64_t r = (int64_t)sqrt(4.0 * (double)n2);
+  while (r * r > 4 * n2) --r;
+  while ((r + 1) * (r + 1) <= 4 * n2) ++r;
+  return (int)((r + 1) / 2);
+}
+
+template <class R>
+__global__ void k_pk_plane(const cplx<R>* __restrict__ spec, int M, const R* __restrict__ gtab, int nbins,
+                           double norm, double shot, double kf, double* __restrict__ part) {
+  extern __shared__ double wrow[];  // [warps][nbins][3]: modes, sum |k|, sum P
+  const int kx = blockIdx.x, HN = M / 2 + 1;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int q = threadIdx.x; q < nw * nbins * 3; q += blockDim.x) wrow[q] = 0.0;
+  __syncthreads();
+  const int sx = kx <= M / 2 ? kx : kx - M;
+  const R* wt = gtab + M;
+  const int64_t nmodes = (int64_t)M * HN;
+  for (int64_t base = (int64_t)w * 32; base < nmodes; base += (int64_t)nw * 32) {
+    const int64_t q = base + lane;
+    int b = 0;
+    double cnt = 0.0, ksum = 0.0, psum = 0.0;
+    if (q < nmodes) {
+      const int ky = (int)(q / HN), kz = (int)(q % HN);
+      const int sy = ky <= M / 2 ? ky : ky - M;
+      const int64_t n2 = (int64_t)sx * sx + (int64_t)sy * sy + (int64_t)kz * kz;
+      b = mode_bin(n2);
+      if (b >= 1 && b <= nbins) {
+        const cplx<R> d = spec[((int64_t)kx * M + ky) * HN + kz];
+        const double wv = (double)wt[kx] * (double)wt[ky] * (double)wt[kz];
+        const double p = ((double)d.x * (double)d.x + (double)d.y * (double)d.y) * norm / (wv * wv) - shot;
+        cnt = (kz == 0 || 2 * kz == M) ? 1.0 : 2.0;
+        ksum = cnt * kf * sqrt((double)n2);
+        psum = cnt * p;
+      } else {
+        b = 0;
+      }
+    }
+    const unsigned same = __match_any_sync(0xffffffffu, b);
+    const int lead = __ffs(same) - 1;
+    double c = 0.0, ks = 0.0, ps = 0.0;
+    for (int l = 0; l < 32; ++l) {  // every lane joins each shuffle; the leader keeps its bin's lanes
+      const double tc = __shfl_sync(0xffffffffu, cnt, l), tk = __shfl_sync(0xffffffffu, ksum, l),
+                   tp = __shfl_sync(0xffffffffu, psum, l);
+      if ((same >> l) & 1u) {
+        c += tc;
+        ks += tk;
+        ps += tp;
+      }
+    }
+    if (lane == lead && b >= 1) {
+      double* row = wrow + ((int64_t)w * nbins + (b - 1)) * 3;
+      row[0] += c;
+      row[1] += ks;
+      row[2] += ps;
+    }
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < nbins * 3; q += blockDim.x) {
+    double s = 0.0;
+    for (int v = 0; v < nw; ++v) s += wrow[(int64_t)v * nbins * 3 + q];
+    part[(int64_t)kx * nbins * 3 + q] = s;
+  }
+}
+
+__global__ void k_pk_final(const double* __restrict__ part, int M, int nbins, double* __restrict__ out) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;  // (bin, field)
+  if (q >= nbins * 3) return;
+  double s = 0.0;
+  for (int kx = 0; kx < M; ++kx) s += part[(int64_t)kx * nbins * 3 + q];
+  out[q] = s;
+}
+
+__global__ void k_sum_k2(const int32_t* __restrict__ d_n, const uint32_t* __restrict__ k,
+                         unsigned long long* __restrict__ out) {
+  const int64_t n = *d_n;
+  unsigned long long s = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    s += (unsigned long long)k[i] * k[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0 && s) atomicAdd(out, s);
+}
+
+template <class R>
+void pk_impl(dzs_ctx* c, int nbins, double* d_part, double* d_out, double shot) {
+  Buffers& B = c->B;
+  const int M = c->M;
+  const int64_t m3 = (int64_t)M * M * M;
+  const int sh = 3 * (kMaxLevel - c->logM);
+  k_cell_start<<<grid_for(c->N0 + 1), kThreads, 0, c->stream>>>(B.n, B.key, sh, m3, B.cell_start);
+  R inv_nbar = (R)((double)m3 / (double)c->N0);
+  k_cic_gather<R><<<(unsigned)(m3 / 512), 256, 0, c->stream>>>(B.cell_start, B.n, c->cap, B.u, B.k, M, (R*)B.rho,
+                                                               inv_nbar);
+  fft_r2c_3d<R>(c, (const R*)B.rho, (cplx<R>*)B.spec, M, (const cplx<R>*)B.twiddle);
+  const double L = c->P.box;
+  const double norm = L * L * L / ((double)m3 * (double)m3);
+  const size_t smem = (size_t)(kPkThreads / 32) * nbins * 3 * sizeof(double);
+  k_pk_plane<R><<<M, kPkThreads, smem, c->stream>>>((const cplx<R>*)B.spec, M, (const R*)B.green_axis, nbins, norm,
+                                                    shot, 2.0 * M_PI / L, d_part);
+  k_pk_final<<<(nbins * 3 + 255) / 256, 256, 0, c->stream>>>(d_part, M, nbins, d_out);
+}
+
 }  // namespace
+
+// P(k) of the current particles: sums of [modes, |k|, P] per bin in d_out
+// [nbins][3]; d_part holds M * nbins * 3 doubles.  The state must be
+// Morton-sorted with valid keys.
+void launch_pk(dzs_ctx* c, int nbins, double* d_part, double* d_out, double shot) {
+  c->launches += c->fp64 ? 7 : 7;
+  if (c->fp64)
+    pk_impl<double>(c, nbins, d_part, d_out, shot);
+  else
+    pk_impl<float>(c, nbins, d_part, d_out, shot);
+}
+
+void launch_sum_k2(dzs_ctx* c, unsigned long long* out) {
+  c->launches += 1;
+  cudaMemsetAsync(out, 0, sizeof(unsigned long long), c->stream);
+  k_sum_k2<<<grid_for(c->N0), kThreads, 0, c->stream>>>(c->B.n, c->B.k, out);
+}
 
 void launch_pm(dzs_ctx* c, bool want_pm) {
   c->launches += want_pm ? 8 : 7;

@@ -185,3 +185,53 @@ def test_observe_errors(dzs):
         ctx.observe()  # off
         with pytest.raises(dzs.DzsError):
             ctx.skymap(4)
+
+
+# ---------------------------------------------------------------- P(k)
+
+def _evolved(upto):
+    P = O.params(**SMALL)
+    st = O.initial_state(P)
+    for n in range(upto):
+        st, _ = O.step(P, n, st)
+    return P, st
+
+
+@pytest.mark.parametrize("precision,tol", [(1, 1e-10), (0, 1e-4)])
+def test_power_spectrum_matches_oracle(dzs, precision, tol):
+    from oracle import pk
+    P, st = _evolved(70)
+    st = dict(st)
+    # shuffle the order: the call must sort internally and restore it
+    perm = np.random.default_rng(1).permutation(st["u"].shape[1])
+    st = {"u": st["u"][:, perm], "p": st["p"][:, perm], "g": st["g"][:, perm], "k": st["k"][perm],
+          "id": st["id"][perm], "fl": st["fl"][perm]}
+    nb = 16
+    wk, wp, wn = pk.power_spectrum(P, st["u"], st["k"], nb)
+    with dzs.Context(**SMALL, precision=precision) as ctx:
+        ctx.set_state(st, 70)
+        before = ctx.state()
+        k, p, n = ctx.power_spectrum(nb)
+        after = ctx.state()
+    for f in before:
+        assert np.array_equal(before[f], after[f]), f
+    assert np.array_equal(n, wn)
+    assert np.allclose(k, wk, rtol=1e-14, atol=0)
+    shot = P.box ** 3 * float((st["k"].astype(float) ** 2).sum()) / float(st["k"].sum()) ** 2
+    assert np.all(np.abs(p - wp) <= tol * (np.abs(wp) + shot)), np.abs(p - wp) / (np.abs(wp) + shot)
+
+
+def test_power_spectrum_full_size_ics(dzs):
+    """128^3 oracle ICs on the 256^3 mesh (the bench workload's first state), FP32"""
+    from oracle import pk
+    kw = dict(n1d=128, mesh=256, box=256.0, merge_level=3, seed=2)
+    P = O.params(**kw)
+    st = O.ics(P)
+    st["fl"] = np.zeros_like(st["k"], np.uint8)
+    wk, wp, wn = pk.power_spectrum(P, st["u"], st["k"], 64)
+    with dzs.Context(**kw, precision=0) as ctx:
+        ctx.set_state(dict(st, p=st["p"], g=np.zeros_like(st["p"])), 0)
+        k, p, n = ctx.power_spectrum(64)
+    shot = P.box ** 3 / 128 ** 3
+    assert np.array_equal(n, wn)
+    assert np.all(np.abs(p - wp) <= 1e-4 * (np.abs(wp) + shot))
