@@ -277,12 +277,17 @@ DZS_API dzs_status dzs_skymap_alm(dzs_ctx* c, int32_t lmax, double* cl, double* 
  * delta = n / nbar - 1, forward FFT, P_mode = |delta_k|^2 L^3 / M^6 / W(k)^2
  * - P_shot with W = prod_i sinc^2(pi n_i / M) and P_shot = L^3 sum k^2 /
  * (sum k)^2; bin b = 1..nbins holds the modes with round(|n|) = b (|n| =
- * |k| L / 2 pi, rounding decided on integers).  k[b] = mean |k| [h/Mpc],
+ * |k| L / 2 pi, rounding decided on integers); P_shot only with
+ * DZS_PK_SHOT in flags.  k[b] = mean |k| [h/Mpc],
  * pk[b] = mean P_mode [(Mpc/h)^3], nmodes[b] = number of modes (k and nmodes
  * may be NULL).  1 <= nbins <= mesh / 2.  Arithmetic in the context's
  * precision, sums in FP64 in a fixed order.  Overwrites the meshes
  * dzs_get_mesh returns; the state and its order are unchanged.  Synchronises. */
-DZS_API dzs_status dzs_power_spectrum(dzs_ctx* c, int32_t nbins, double* k, double* pk, double* nmodes);
+DZS_API dzs_status dzs_power_spectrum(dzs_ctx* c, int32_t nbins, int32_t flags, double* k, double* pk,
+                                      double* nmodes);
+/* flags of dzs_power_spectrum: subtract P_shot (meant for Poisson-like sets;
+ * merged particles, one per cell, and a displaced lattice are not) */
+enum { DZS_PK_SHOT = 1 };
 
 DZS_API dzs_status dzs_get_tables(dzs_ctx* c, double* a, double* drift, double* kick1, double* kick2,
                           double* rlc, uint64_t* rlat);

@@ -9,7 +9,8 @@ delta = n / nbar - 1 on the nodes iL/M):
     delta_k = sum_x delta(x) e^{-i k.x}              (numpy.fft.fftn, all modes)
     P_mode  = |delta_k|^2 L^3 / M^6 / W(k)^2 - P_shot
     W(k)    = prod_i sinc^2(pi n_i / M)              (CIC assignment window)
-    P_shot  = L^3 sum k_j^2 / (sum k_j)^2             (particles of mass k_j m0)
+    P_shot  = L^3 sum k_j^2 / (sum k_j)^2             (particles of mass k_j m0;
+                                                       optional: meant for Poisson-like sets)
 Bins: mode n (integer vector, |n| = |k| / k_f, k_f = 2 pi / L) belongs to bin
 b = round(|n|), i.e. (b - 1/2)^2 <= |n|^2 < (b + 1/2)^2 tested on integers;
 b = 1 .. nbins.  Per bin: the number of modes, the mean |k| and the mean
@@ -56,10 +57,10 @@ def pk_from_delta(P, delta, nbins, shot=0.0, deconvolve=True):
     return out_k, out_p, out_n
 
 
-def power_spectrum(P, u, k, nbins):
+def power_spectrum(P, u, k, nbins, subtract_shot=True):
     """(k, P(k), modes) of the particles u [3, n] (uint32 lattice), masses k"""
     k = np.asarray(k)
     delta = cic_delta(P, u, k).reshape(P.mesh, P.mesh, P.mesh)
     kk = k.astype(np.float64)
-    shot = P.box ** 3 * float((kk * kk).sum()) / float(kk.sum()) ** 2
+    shot = P.box ** 3 * float((kk * kk).sum()) / float(kk.sum()) ** 2 if subtract_shot else 0.0
     return pk_from_delta(P, delta, nbins, shot=shot)

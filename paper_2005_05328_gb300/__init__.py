@@ -28,6 +28,7 @@ FL_CROSSED, FL_MERGED = 1, 2
 STAGE_KICK_DRIFT, STAGE_SORT, STAGE_MERGE, STAGE_FORCE, STAGE_CLOSE, STAGE_ALL = 1, 2, 4, 8, 16, 31
 ACC_PM, ACC_TREE, ACC_ALL = 1, 2, 3
 MESH_DELTA, MESH_PHI = 0, 1
+PK_SHOT = 1
 
 EXPORTED = ["dzs_params_default", "dzs_footprint_bytes", "dzs_create", "dzs_ics", "dzs_step",
             "dzs_run_stages", "dzs_lightcone_drain", "dzs_destroy", "dzs_get_count", "dzs_get_state",
@@ -105,7 +106,7 @@ def load(path: str = LIB_PATH):
         "dzs_step_until": [vp, i32, C.POINTER(Halt), C.POINTER(i32), C.POINTER(i32), C.POINTER(C.c_double)],
         "dzs_observe_enable": [vp, C.POINTER(Observe)], "dzs_observe_add_records": [vp, vp, sz],
         "dzs_skymap_get": [vp, vp, sz], "dzs_lcdensity_get": [vp, vp, sz],
-        "dzs_skymap_alm": [vp, i32, vp, vp], "dzs_power_spectrum": [vp, i32, vp, vp, vp],
+        "dzs_skymap_alm": [vp, i32, vp, vp], "dzs_power_spectrum": [vp, i32, i32, vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -311,10 +312,10 @@ def dzs_skymap_alm(h, lmax):
     return cl, a
 
 
-def dzs_power_spectrum(h, nbins):
+def dzs_power_spectrum(h, nbins, shot=True):
     """-> (k [h/Mpc], P(k) [(Mpc/h)^3], modes) per bin"""
     k, p, n = np.zeros(nbins), np.zeros(nbins), np.zeros(nbins)
-    _check(load().dzs_power_spectrum(h, nbins, _ptr(k), _ptr(p), _ptr(n)), h)
+    _check(load().dzs_power_spectrum(h, nbins, PK_SHOT if shot else 0, _ptr(k), _ptr(p), _ptr(n)), h)
     return k, p, n
 
 
@@ -373,4 +374,4 @@ class Context:
     def skymap(self, nside): return dzs_skymap_get(self.h, nside)
     def lcdensity(self, mesh): return dzs_lcdensity_get(self.h, mesh)
     def skymap_alm(self, lmax): return dzs_skymap_alm(self.h, lmax)
-    def power_spectrum(self, nbins): return dzs_power_spectrum(self.h, nbins)
+    def power_spectrum(self, nbins, shot=True): return dzs_power_spectrum(self.h, nbins, shot)

@@ -935,11 +935,12 @@ dzs_status dzs_skymap_alm(dzs_ctx* c, int32_t lmax, double* cl, double* alm) {
   return check_device_errors(c);
 }
 
-dzs_status dzs_power_spectrum(dzs_ctx* c, int32_t nbins, double* k, double* pk, double* nmodes) {
+dzs_status dzs_power_spectrum(dzs_ctx* c, int32_t nbins, int32_t flags, double* k, double* pk, double* nmodes) {
   dzs_status s = guard(c);
   if (s) return s;
   if (!c->have_state) return fail(c, DZS_ESTATE, "no particle state");
-  if (nbins < 1 || nbins > c->M / 2 || !pk) return fail(c, DZS_EINVAL, "need 1 <= nbins <= mesh / 2, pk");
+  if (nbins < 1 || nbins > c->M / 2 || !pk || (flags & ~DZS_PK_SHOT))
+    return fail(c, DZS_EINVAL, "need 1 <= nbins <= mesh / 2, pk, known flags");
   // shot noise L^3 sum k^2 / (sum k)^2; sum k = N0 (mass is conserved exactly)
   unsigned long long* k2 = (unsigned long long*)(c->B.counters + 15);
   launch_sum_k2(c, k2);
@@ -947,7 +948,7 @@ dzs_status dzs_power_spectrum(dzs_ctx* c, int32_t nbins, double* k, double* pk, 
   CK(cudaMemcpyAsync(&sk2, k2, sizeof sk2, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   const double L = c->P.box, n0 = (double)c->N0;
-  const double shot = L * L * L * (double)sk2 / (n0 * n0);
+  const double shot = (flags & DZS_PK_SHOT) ? L * L * L * (double)sk2 / (n0 * n0) : 0.0;
   // CIC needs the Morton order: sort, bin, then put the state back in its order
   // (g is not moved by either, so it stays with its particles)
   double* part = (double*)c->B.phi;  // mesh scratch: M nbins 3 + nbins 3 doubles

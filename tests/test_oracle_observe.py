@@ -254,15 +254,43 @@ def test_pk_poisson_sample():
 
 def test_pk_of_initial_conditions_is_linear_theory():
     """the ICs' particles at z = 49 follow P_lin(k) D+(a_i)^2 bin by bin.  A
-    displaced lattice carries no Poisson shot noise, so the subtracted P_shot
-    is added back here (the subtraction is meant for evolved, Poisson-like
-    particle sets)"""
+    displaced lattice carries no Poisson shot noise: nothing is subtracted"""
     from oracle import pk
     P = O.params(n1d=32, mesh=64, box=256.0, seed=3)
     st = O.ics(P)
-    k, p, nm = pk.power_spectrum(P, st["u"], st["k"], 12)
-    p = p + P.box ** 3 / 32 ** 3
+    k, p, nm = pk.power_spectrum(P, st["u"], st["k"], 12, subtract_shot=False)
     D = O.growth(P, 1 / 50)
     for j in range(12):
         want = O.power(P, k[j]) * D * D
         assert abs(p[j] / want - 1) < 5 * math.sqrt(2.0 / nm[j]), (j, p[j], want)
+
+
+
+def test_dzs_vs_std_lightcone_within_paper_accuracy():
+    """Sec. 3.1.2: the sky-projected lightcone of a DZS run matches the
+    standard run's to <= 0.1% (here identical, like the paper's SMALL pair);
+    the 3D lightcone and the angular power spectrum too.  16^3, L = 32, FP64
+    oracle, full runs from the same ICs."""
+    def run(P):
+        st = O.initial_state(P)
+        recs = []
+        for n in range(P.nsteps):
+            st, rec = O.step(P, n, st)
+            recs.append(rec)
+        return st, np.concatenate(recs)
+    kw = dict(n1d=16, mesh=32, box=32.0, merge_level=2)
+    std_st, std_rec = run(O.params(**kw, dzs_on=0))
+    dzs_st, dzs_rec = run(O.params(**kw, dzs_on=1))
+    P = O.params(**kw)
+    assert dzs_st["u"].shape[1] < 0.6 * std_st["u"].shape[1]  # DZS did de-refine
+    assert dzs_rec["k"].sum() == std_rec["k"].sum() == 16 ** 3
+    for nside in (4, 16):
+        a = O.skymap(P, std_rec, nside).astype(float)
+        b = O.skymap(P, dzs_rec, nside).astype(float)
+        assert np.abs(a - b).sum() <= 1e-3 * a.sum()
+    ga = O.lcdensity(P, std_rec, 16).astype(float)
+    gb = O.lcdensity(P, dzs_rec, 16).astype(float)
+    assert np.abs(ga - gb).sum() <= 1e-3 * ga.sum()
+    ca = sht.cl(sht.alm(O.skymap(P, std_rec, 8).astype(float), 8, 16))
+    cb = sht.cl(sht.alm(O.skymap(P, dzs_rec, 8).astype(float), 8, 16))
+    assert np.all(np.abs(cb / ca - 1) <= 1e-3)
