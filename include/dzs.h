@@ -289,6 +289,51 @@ DZS_API dzs_status dzs_power_spectrum(dzs_ctx* c, int32_t nbins, int32_t flags, 
  * merged particles, one per cell, and a displaced lattice are not) */
 enum { DZS_PK_SHOT = 1 };
 
+/* ---- Serving: continuous batching of independent lightcone mocks ----
+ * No counterpart in the paper, which runs one simulation per MPI job; it
+ * extends the paper's point that a DZS run needs less memory as it goes
+ * (Sec. 4.1.1) to many mocks sharing one GPU.  Each request becomes a context
+ * with its own non-blocking stream, admitted in arrival order once the sum of
+ * the admitted footprints (dzs_footprint_bytes) fits hbm_budget_bytes (and
+ * at most max_active run at once), advanced in slices of steps_per_slice
+ * steps that overlap on the device, drained at a = 1 and destroyed (its
+ * memory returns to the budget).  A mock's result does not depend on the mix
+ * (separate state, deterministic reductions); record_hash (FNV-1a of the
+ * drained records) lets a caller check that. */
+typedef struct {
+  double arrival_s; /* seconds after the start of dzs_serve */
+  int32_t n1d;      /* particles per side */
+  int32_t mesh;     /* PM mesh per side */
+  double box;       /* L [Mpc/h] */
+  double sigma8;
+  uint64_t seed;
+} dzs_request;
+
+typedef struct {
+  double admit_s, done_s; /* seconds after the start (latency = done_s - arrival_s) */
+  uint64_t n_end;         /* particles left at a = 1 */
+  uint64_t records;       /* lightcone records */
+  uint64_t record_hash;   /* FNV-1a 64 of the records in drain order */
+  double diag[8];         /* dzs_diagnostics at a = 1 */
+  int32_t status;         /* dzs_status of this request */
+  int32_t reserved_;
+} dzs_request_result;
+
+typedef struct {
+  double hbm_budget_bytes;
+  int32_t max_active;      /* 0: no limit besides the budget */
+  int32_t steps_per_slice; /* >= 1 */
+  dzs_params base;         /* everything but n1d, mesh, box, sigma8, seed (capacity ignored) */
+} dzs_serve_config;
+
+/* Serve n requests (any order of arrival_s) to completion on base.device;
+ * out[i] belongs to req[i].  Returns DZS_OK, or the first failing status (the
+ * other requests still run); a request that alone exceeds the budget gets
+ * DZS_ENOMEM.  *wall_s (may be NULL) = seconds from start to the last
+ * completion.  The calling thread drives the loop until every request is done. */
+DZS_API dzs_status dzs_serve(const dzs_serve_config* cfg, const dzs_request* req, size_t n,
+                             dzs_request_result* out, double* wall_s);
+
 DZS_API dzs_status dzs_get_tables(dzs_ctx* c, double* a, double* drift, double* kick1, double* kick2,
                           double* rlc, uint64_t* rlat);
 

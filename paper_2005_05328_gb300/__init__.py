@@ -36,7 +36,7 @@ EXPORTED = ["dzs_params_default", "dzs_footprint_bytes", "dzs_create", "dzs_ics"
             "dzs_get_mesh", "dzs_get_counters", "dzs_set_profiling", "dzs_get_profile",
             "dzs_morton_sort_noalloc", "dzs_checkpoint_bytes", "dzs_checkpoint", "dzs_restore",
             "dzs_step_until", "dzs_observe_enable", "dzs_observe_add_records", "dzs_skymap_get",
-            "dzs_lcdensity_get", "dzs_skymap_alm", "dzs_power_spectrum", "dzs_last_error"]
+            "dzs_lcdensity_get", "dzs_skymap_alm", "dzs_power_spectrum", "dzs_serve", "dzs_last_error"]
 NOALLOC_SORT_MAX_N = 262144
 PROF_NAMES = ["kick_drift", "sort", "merge", "tree", "pm", "walk"]
 
@@ -61,6 +61,22 @@ class Halt(C.Structure):
 
 
 HALT_NONE, HALT_RATIO, HALT_PREDICTED, HALT_WALL = 0, 1, 2, 3
+
+
+class Request(C.Structure):
+    _fields_ = [("arrival_s", C.c_double), ("n1d", C.c_int32), ("mesh", C.c_int32), ("box", C.c_double),
+                ("sigma8", C.c_double), ("seed", C.c_uint64)]
+
+
+class RequestResult(C.Structure):
+    _fields_ = [("admit_s", C.c_double), ("done_s", C.c_double), ("n_end", C.c_uint64),
+                ("records", C.c_uint64), ("record_hash", C.c_uint64), ("diag", C.c_double * 8),
+                ("status", C.c_int32), ("reserved_", C.c_int32)]
+
+
+class ServeConfig(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_double), ("max_active", C.c_int32), ("steps_per_slice", C.c_int32),
+                ("base", Params)]
 
 
 class Observe(C.Structure):
@@ -107,6 +123,7 @@ def load(path: str = LIB_PATH):
         "dzs_observe_enable": [vp, C.POINTER(Observe)], "dzs_observe_add_records": [vp, vp, sz],
         "dzs_skymap_get": [vp, vp, sz], "dzs_lcdensity_get": [vp, vp, sz],
         "dzs_skymap_alm": [vp, i32, vp, vp], "dzs_power_spectrum": [vp, i32, i32, vp, vp, vp],
+        "dzs_serve": [C.POINTER(ServeConfig), vp, sz, vp, C.POINTER(C.c_double)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -317,6 +334,28 @@ def dzs_power_spectrum(h, nbins, shot=True):
     k, p, n = np.zeros(nbins), np.zeros(nbins), np.zeros(nbins)
     _check(load().dzs_power_spectrum(h, nbins, PK_SHOT if shot else 0, _ptr(k), _ptr(p), _ptr(n)), h)
     return k, p, n
+
+
+def dzs_serve(requests, hbm_budget_bytes, max_active=0, steps_per_slice=8, **base):
+    """requests: iterable of dicts (arrival_s, n1d, mesh, box, sigma8, seed).
+    -> (status, wall seconds, list of result dicts with arrival_s and latency_s)"""
+    reqs = list(requests)
+    arr = (Request * max(1, len(reqs)))()
+    for i, r in enumerate(reqs):
+        arr[i] = Request(float(r["arrival_s"]), int(r["n1d"]), int(r["mesh"]), float(r["box"]),
+                         float(r["sigma8"]), int(r["seed"]))
+    res = (RequestResult * max(1, len(reqs)))()
+    cfg = ServeConfig(float(hbm_budget_bytes), int(max_active), int(steps_per_slice), params(**base))
+    wall = C.c_double(0)
+    st = load().dzs_serve(C.byref(cfg), C.cast(arr, C.c_void_p), len(reqs), C.cast(res, C.c_void_p),
+                          C.byref(wall))
+    out = []
+    for i, r in enumerate(reqs):
+        x = res[i]
+        out.append(dict(arrival_s=float(r["arrival_s"]), admit_s=x.admit_s, done_s=x.done_s,
+                        latency_s=x.done_s - float(r["arrival_s"]), n_end=x.n_end, records=x.records,
+                        record_hash=x.record_hash, diag=list(x.diag), status=x.status))
+    return st, wall.value, out
 
 
 def dzs_step_until(h, max_steps: int, ratio_min=0.0, wall_limit_s=0.0, horizon_s=0.0):

@@ -116,13 +116,16 @@ void launch_ics(dzs_ctx* c) {
   const int n1 = c->n1;
   const int64_t n = c->N0, hn = n1 / 2 + 1;
   const int64_t nspec = (int64_t)n1 * n1 * hn;
-  double* w = nullptr;
-  cplx<double>*sd = nullptr, *sw = nullptr, *tw = nullptr;
-  cudaMalloc(&w, sizeof(double) * n);
-  cudaMalloc(&sd, sizeof(cplx<double>) * nspec);
-  cudaMalloc(&sw, sizeof(cplx<double>) * nspec);
+  // scratch from the arena (no allocation, so no device-wide synchronisation
+  // while other contexts run): the noise / displacement grid and the IC
+  // twiddles in the conversion scratch (24 N0 bytes), the two half spectra
+  // (16 n1^2 (n1/2 + 1) <= 12 N0 bytes each for n1 >= 4) in g and gsave,
+  // which the first force evaluation overwrites
+  double* w = (double*)c->B.convert;
+  cplx<double>* tw = (cplx<double>*)(w + n);
+  cplx<double>* sd = (cplx<double>*)c->B.g;
+  cplx<double>* sw = (cplx<double>*)c->B.gsave;
   auto twh = twiddles<double>(n1);
-  cudaMalloc(&tw, sizeof(cplx<double>) * twh.size());
   cudaMemcpyAsync(tw, twh.data(), sizeof(cplx<double>) * twh.size(), cudaMemcpyHostToDevice, c->stream);
   k_noise<<<grid_for(n), kThreads, 0, c->stream>>>(c->P.seed, n, w);
   fft_r2c_3d<double>(c, w, sd, n1, tw);
@@ -148,11 +151,6 @@ void launch_ics(dzs_ctx* c) {
   }
   uint64_t r0 = c->T.rlat[0];
   k_ics_finish<<<grid_for(n), kThreads, 0, c->stream>>>(n, c->cap, c->B.u, c->B.k, c->B.id, c->B.fl, r0 * r0, c->B.n);
-  cudaStreamSynchronize(c->stream);
-  cudaFree(w);
-  cudaFree(sd);
-  cudaFree(sw);
-  cudaFree(tw);
 }
 
 }  // namespace dzs

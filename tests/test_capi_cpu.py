@@ -91,6 +91,11 @@ def test_struct_layouts_match_the_header(tmp_path, dzs):
     obs = [f[0] for f in dzs.Observe._fields_]
     body += ['  printf("%zu\\n", sizeof(dzs_observe));']
     body += ['  printf("%%zu\\n", offsetof(dzs_observe, %s));' % f for f in obs]
+    extra = [("dzs_request", dzs.Request), ("dzs_request_result", dzs.RequestResult),
+             ("dzs_serve_config", dzs.ServeConfig)]
+    for cname, cls in extra:
+        body += ['  printf("%%zu\\n", sizeof(%s));' % cname]
+        body += ['  printf("%%zu\\n", offsetof(%s, %s));' % (cname, f[0]) for f in cls._fields_]
     body += ['  printf("%zu\\n", sizeof(dzs_lc_record));', "  return 0;", "}"]
     src = tmp_path / "layout.c"
     src.write_text("\n".join(body) + "\n")
@@ -100,5 +105,7 @@ def test_struct_layouts_match_the_header(tmp_path, dzs):
     want = [ctypes.sizeof(dzs.Params)] + [getattr(dzs.Params, f).offset for f in fields]
     want += [ctypes.sizeof(dzs.Halt)] + [getattr(dzs.Halt, f).offset for f in halt]
     want += [ctypes.sizeof(dzs.Observe)] + [getattr(dzs.Observe, f).offset for f in obs]
+    for cname, cls in extra:
+        want += [ctypes.sizeof(cls)] + [getattr(cls, f[0]).offset for f in cls._fields_]
     want += [dzs.RECORD_DTYPE.itemsize]
     assert got == want
