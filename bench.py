@@ -45,8 +45,80 @@ STAGE_BYTES = {
     "sort": lambda n, m3: 326 * n,
     "merge": lambda n, m3: 194 * n,
     "tree": lambda n, m3: 95 * n,
-    "pm": lambda n, m3: 56.3 * m3 + 40 * n,
+    # CIC deposit (cell bounds 8 B, delta 4 B per cell; u, k 16 B per particle)
+    # and gradient + interpolation (phi 4 B per cell; u 12 B in, g 12 B out)
+    "pm": lambda n, m3: 16.0 * m3 + 40 * n,
+    # five passes over the mesh: Z r2c, Y, X with the Green multiply, Y^-1, Z c2r
+    "fft": lambda n, m3: 40.3 * m3,
 }
+
+# serving sample (Poisson stream of mock requests, sizes 32^3 .. 256^3)
+SERVE_RATE = 4.0
+SERVE_SIZES = (32, 64, 128, 256)
+SERVE_BUDGET = 150e9
+
+
+def splitmix64(state):
+    """SplitMix64 (Steele, Lea & Flood 2014): returns (next state, output)"""
+    state = (state + 0x9E3779B97F4A7C15) & 0xFFFFFFFFFFFFFFFF
+    z = state
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & 0xFFFFFFFFFFFFFFFF
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & 0xFFFFFFFFFFFFFFFF
+    return state, z ^ (z >> 31)
+
+
+def serve_requests(n, seed=5, rate=SERVE_RATE):
+    """Poisson arrivals (exponential gaps), N1 uniform over SERVE_SIZES,
+    L = 2 N1 Mpc/h, mesh 2 N1, sigma8 uniform in [0.7, 0.9], random seeds."""
+    st, t, out = seed, 0.0, []
+    for i in range(n):
+        st, a = splitmix64(st)
+        st, b = splitmix64(st)
+        st, c = splitmix64(st)
+        st, d = splitmix64(st)
+        t += -np.log1p(-(a >> 11) / 2.0 ** 53) / rate
+        n1 = SERVE_SIZES[b % len(SERVE_SIZES)]
+        out.append(dict(arrival_s=t, n1d=n1, mesh=2 * n1, box=2.0 * n1, sigma8=0.7 + 0.2 * (c >> 11) / 2.0 ** 53,
+                        seed=int(d % (2 ** 31 - 1)) + 1))
+    return out
+
+
+def serving_sample(dzs, nreq, warm):
+    """C ABI serving loop over a bounded Poisson stream; latency statistics
+    over the requests after the first `warm` ones."""
+    reqs = serve_requests(nreq + warm)
+    st, wall, res = dzs.dzs_serve(reqs, hbm_budget_bytes=SERVE_BUDGET, steps_per_slice=8, precision=dzs.FP32)
+    lat = sorted(r["latency_s"] for r in res[warm:])
+    work = sum(q["n1d"] ** 3 * 96 for q in reqs)
+    offered = SERVE_RATE * float(np.mean([n ** 3 for n in SERVE_SIZES])) * 96
+    return {"requests": nreq, "warmup_requests": warm, "status": st, "rate_per_s": SERVE_RATE,
+            "hbm_budget_GB": SERVE_BUDGET / 1e9, "wall_s": wall,
+            "mocks_per_h": 3600.0 * len(res) / wall,
+            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+            "effective_particle_steps_per_s": work / wall,
+            "offered_particle_steps_per_s": offered,
+            "note": "offered load of the stream vs what the GPU sustained; when offered > sustained the queue "
+                    "grows and p99 grows with the number of requests (no steady state)"}
+
+
+def cufft_compare(stream, M, iters=20):
+    """cuFFT (through torch.fft) r2c + Green-like multiply + c2r of an M^3 FP32
+    mesh, the library comparison for the hand-written FFT stage"""
+    import torch
+    with torch.cuda.stream(stream):
+        x = torch.randn(M, M, M, device="cuda", dtype=torch.float32)
+        g = torch.rand(M, M, M // 2 + 1, device="cuda", dtype=torch.float32)
+        for _ in range(3):
+            y = torch.fft.irfftn(torch.fft.rfftn(x) * g, s=(M, M, M))
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(iters):
+            y = torch.fft.irfftn(torch.fft.rfftn(x) * g, s=(M, M, M))
+        b.record(stream)
+        b.synchronize()
+    del y
+    return a.elapsed_time(b) / iters
 
 
 def active_counts(dzs, P, stream, warmup, steps):
@@ -230,6 +302,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the plain-FP64 and no-DZS runs")
+    ap.add_argument("--serve-requests", type=int, default=24, help="serving sample size (0: skip)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -377,7 +450,14 @@ def main():
             comp[name] = {"value": n0 * k / sec if sec > 0 else None, "unit": UNIT, "steps_timed": k,
                           "ms_per_step": 1e3 * sec / max(1, k),
                           "ratio_dzs_fp32_over_this": (value / (n0 * k / sec)) if sec > 0 else None}
+        fft_ms = prof["fft"][0] / max(1, prof["fft"][1])
+        cu = cufft_compare(stream, P.mesh)
+        comp["cufft_256cubed_r2c_green_c2r"] = {"ms": cu, "ours_ms": fft_ms, "ours_over_cufft_time": fft_ms / cu,
+                                                "note": "torch.fft (cuFFT) rfftn * G + irfftn, FP32, same mesh"}
         line["comparisons"] = comp
+    line["config"]["mocks_per_h_single_stream"] = 3600.0 / (P.nsteps * ms / args.steps / 1e3)
+    if world == 1 and args.serve_requests > 0:
+        line["serving"] = serving_sample(dzs, args.serve_requests, 4)
     if world == 1 and not args.no_cpu_baseline:
         try:
             line["cpu_baseline"] = cpu_baseline()

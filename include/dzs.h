@@ -355,9 +355,10 @@ enum {
   DZS_PROF_SORT = 1,       /* radix sort + permutation */
   DZS_PROF_MERGE = 2,      /* DZS merge */
   DZS_PROF_TREE = 3,       /* tree build + group list */
-  DZS_PROF_PM = 4,         /* CIC deposit, FFT Poisson solve, gradient + interpolation */
+  DZS_PROF_PM = 4,         /* CIC deposit; four-point gradient + CIC interpolation */
   DZS_PROF_WALK = 5,       /* tree walk + closing kick */
-  DZS_PROF_N = 6
+  DZS_PROF_FFT = 6,        /* FFT Poisson solve (r2c, Green multiply, c2r) */
+  DZS_PROF_N = 7
 };
 
 /* Enable (1) or disable (0) per-stage CUDA-event timing on the context

@@ -38,7 +38,7 @@ EXPORTED = ["dzs_params_default", "dzs_footprint_bytes", "dzs_create", "dzs_ics"
             "dzs_step_until", "dzs_observe_enable", "dzs_observe_add_records", "dzs_skymap_get",
             "dzs_lcdensity_get", "dzs_skymap_alm", "dzs_power_spectrum", "dzs_serve", "dzs_last_error"]
 NOALLOC_SORT_MAX_N = 262144
-PROF_NAMES = ["kick_drift", "sort", "merge", "tree", "pm", "walk"]
+PROF_NAMES = ["kick_drift", "sort", "merge", "tree", "pm", "walk", "fft"]
 
 
 class Params(C.Structure):

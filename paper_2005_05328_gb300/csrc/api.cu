@@ -219,12 +219,19 @@ void run_force(dzs_ctx* c, int parts, bool close_kick) {
     ProfScope ps(c, DZS_PROF_TREE);
     launch_tree(c);  // also lists the groups the walk needs
   }
-  {
+  if (parts & DZS_ACC_PM) {
+    {
+      ProfScope ps(c, DZS_PROF_PM);
+      launch_pm_deposit(c);
+    }
+    {
+      ProfScope ps(c, DZS_PROF_FFT);
+      launch_pm_fft(c);
+    }
     ProfScope ps(c, DZS_PROF_PM);
-    if (parts & DZS_ACC_PM)
-      launch_pm(c, true);
-    else
-      cudaMemsetAsync(c->B.g, 0, 3 * c->cap * (c->fp64 ? 8 : 4), c->stream);
+    launch_pm_interp(c);
+  } else {
+    cudaMemsetAsync(c->B.g, 0, 3 * c->cap * (c->fp64 ? 8 : 4), c->stream);
   }
   ProfScope ps(c, DZS_PROF_WALK);
   launch_walk(c, (parts & DZS_ACC_TREE) != 0, close_kick, c->step);

@@ -206,7 +206,9 @@ void launch_close_kick(dzs_ctx* c, int step);
 void launch_merge(dzs_ctx* c, uint64_t rlat);
 void launch_amin2(dzs_ctx* c);
 void launch_tree(dzs_ctx* c);
-void launch_pm(dzs_ctx* c, bool want_pm);
+void launch_pm_deposit(dzs_ctx* c);
+void launch_pm_fft(dzs_ctx* c);
+void launch_pm_interp(dzs_ctx* c);
 void launch_walk(dzs_ctx* c, bool tree, bool close_kick, int step);
 void launch_diagnostics(dzs_ctx* c);
 void launch_ics(dzs_ctx* c);

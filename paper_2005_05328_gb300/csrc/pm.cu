@@ -118,7 +118,7 @@ __global__ void k_pm_interp(const int32_t* __restrict__ d_n, int64_t cap, const 
 }
 
 template <class R>
-void pm_impl(dzs_ctx* c, bool want_pm) {
+void pm_deposit(dzs_ctx* c) {
   Buffers& B = c->B;
   const int M = c->M;
   const int64_t m3 = (int64_t)M * M * M;
@@ -127,15 +127,26 @@ void pm_impl(dzs_ctx* c, bool want_pm) {
   double n0 = (double)c->N0;
   R inv_nbar = (R)((double)m3 / n0);
   k_cic_gather<R><<<(unsigned)(m3 / 512), 256, 0, c->stream>>>(B.cell_start, B.n, c->cap, B.u, B.k, M, (R*)B.rho, inv_nbar);
+}
+
+template <class R>
+void pm_fft(dzs_ctx* c) {
+  Buffers& B = c->B;
+  const int M = c->M;
+  const int64_t m3 = (int64_t)M * M * M;
   const cplx<R>* tw = (const cplx<R>*)B.twiddle;
   fft_r2c_zy<R>(c, (const R*)B.rho, (cplx<R>*)B.spec, M, tw);
   R gfac = (R)(-1.5 * c->P.omega_m / (double)m3);
   fft_c2r_3d<R>(c, (cplx<R>*)B.spec, (R*)B.phi, M, tw, (const R*)B.green_axis, gfac);
-  if (want_pm) {
-    R inv12dx = (R)(1.0 / (12.0 * c->P.box / M));
-    k_pm_interp<R><<<grid_for(c->N0), kThreads, 0, c->stream>>>(B.n, c->cap, B.u, (const R*)B.phi, M, inv12dx,
-                                                                (R*)B.g);
-  }
+}
+
+template <class R>
+void pm_interp(dzs_ctx* c) {
+  Buffers& B = c->B;
+  const int M = c->M;
+  R inv12dx = (R)(1.0 / (12.0 * c->P.box / M));
+  k_pm_interp<R><<<grid_for(c->N0), kThreads, 0, c->stream>>>(B.n, c->cap, B.u, (const R*)B.phi, M, inv12dx,
+                                                              (R*)B.g);
 }
 
 // ---- 3D power spectrum of the mesh (forward spectrum of the CIC delta)
@@ -270,12 +281,31 @@ void launch_sum_k2(dzs_ctx* c, unsigned long long* out) {
   k_sum_k2<<<grid_for(c->N0), kThreads, 0, c->stream>>>(c->B.n, c->B.k, out);
 }
 
-void launch_pm(dzs_ctx* c, bool want_pm) {
-  c->launches += want_pm ? 8 : 7;
+// the PM force in three stages: CIC deposit of delta; FFT Poisson solve with
+// the Green function fused into the X pass (phi); four-point gradient and
+// CIC interpolation to the particles (g)
+void launch_pm_deposit(dzs_ctx* c) {
+  c->launches += 2;
   if (c->fp64)
-    pm_impl<double>(c, want_pm);
+    pm_deposit<double>(c);
   else
-    pm_impl<float>(c, want_pm);
+    pm_deposit<float>(c);
+}
+
+void launch_pm_fft(dzs_ctx* c) {
+  c->launches += 5;
+  if (c->fp64)
+    pm_fft<double>(c);
+  else
+    pm_fft<float>(c);
+}
+
+void launch_pm_interp(dzs_ctx* c) {
+  c->launches += 1;
+  if (c->fp64)
+    pm_interp<double>(c);
+  else
+    pm_interp<float>(c);
 }
 
 template <class R>

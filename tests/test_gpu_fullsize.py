@@ -96,3 +96,28 @@ def test_gpu_run_invariants(dzs):
     assert len(ids) == n0 and len(np.unique(ids)) == n0
     assert n < n0 // 4  # most of the box ends outside the lightcone and is merged
     assert cnt[3] == 0
+
+
+@pytest.mark.parametrize("kw,run", [
+    # the largest serving size: 256^3 in 512 Mpc/h, mesh 512^3, the full 96 steps
+    (dict(n1d=256, mesh=512, box=512.0, merge_level=3, seed=7, nsteps=96), 96),
+    # 512^3 in 1024 Mpc/h, mesh 512^3, 128 steps, merge level 4, the SWEEP
+    # lightcone: the first 40 steps (z = 49 -> 7; crossings and merges under way)
+    (dict(n1d=512, mesh=512, box=1024.0, merge_level=4, seed=3, nsteps=128), 40),
+])
+def test_large_instance_invariants(dzs, kw, run):
+    n0 = kw["n1d"] ** 3
+    with dzs.Context(**kw, precision=0) as ctx:
+        ctx.ics()
+        for _ in range(run // 8):
+            ctx.step(8)
+            d = ctx.diagnostics()
+            assert d[0] == n0  # mass, exactly
+        rec = ctx.drain(cap=n0)
+        n, step = ctx.count()
+        cnt = ctx.counters()
+    ids = rec["id"]
+    assert step == run
+    assert len(np.unique(ids)) == len(ids) > 0
+    assert n < n0
+    assert cnt[3] == 0
