@@ -109,6 +109,8 @@ struct Buffers {
   Node* nodes = nullptr;
   int32_t* lvl_count = nullptr;  // [kMaxLevel + 2]
   uint64_t* nsum = nullptr;      // [3][node cap] scratch sums
+  int32_t* parent = nullptr;     // [node cap] parent node (-1 at the root)
+  int32_t* arrive = nullptr;     // [node cap] children finished (bottom-up pass)
   int32_t* groups = nullptr;     // [cap]
   void* wpm = nullptr;           // real [cap]: G m / s^2 per particle (walk, lattice units)
   void* wph = nullptr;           // real [cap]: spline radius per particle (lattice units)
@@ -206,6 +208,7 @@ void launch_close_kick(dzs_ctx* c, int step);
 void launch_merge(dzs_ctx* c, uint64_t rlat);
 void launch_amin2(dzs_ctx* c);
 void launch_tree(dzs_ctx* c);
+void launch_cell_start(dzs_ctx* c);
 void launch_pm_deposit(dzs_ctx* c);
 void launch_pm_fft(dzs_ctx* c);
 void launch_pm_interp(dzs_ctx* c);

@@ -117,13 +117,12 @@ __global__ void k_pm_interp(const int32_t* __restrict__ d_n, int64_t cap, const 
   }
 }
 
+// the deposit reads the depth-m cell table the tree build wrote for the same keys
 template <class R>
 void pm_deposit(dzs_ctx* c) {
   Buffers& B = c->B;
   const int M = c->M;
   const int64_t m3 = (int64_t)M * M * M;
-  int sh = 3 * (kMaxLevel - c->logM);
-  k_cell_start<<<grid_for(c->N0 + 1), kThreads, 0, c->stream>>>(B.n, B.key, sh, m3, B.cell_start);
   double n0 = (double)c->N0;
   R inv_nbar = (R)((double)m3 / n0);
   k_cic_gather<R><<<(unsigned)(m3 / 512), 256, 0, c->stream>>>(B.cell_start, B.n, c->cap, B.u, B.k, M, (R*)B.rho, inv_nbar);
@@ -284,8 +283,16 @@ void launch_sum_k2(dzs_ctx* c, unsigned long long* out) {
 // the PM force in three stages: CIC deposit of delta; FFT Poisson solve with
 // the Green function fused into the X pass (phi); four-point gradient and
 // CIC interpolation to the particles (g)
+// CSR table of the depth-m Morton cells (m = log2 M) of the current keys
+void launch_cell_start(dzs_ctx* c) {
+  c->launches += 1;
+  const int64_t m3 = (int64_t)c->M * c->M * c->M;
+  const int sh = 3 * (kMaxLevel - c->logM);
+  k_cell_start<<<grid_for(c->N0 + 1), kThreads, 0, c->stream>>>(c->B.n, c->B.key, sh, m3, c->B.cell_start);
+}
+
 void launch_pm_deposit(dzs_ctx* c) {
-  c->launches += 2;
+  c->launches += 1;
   if (c->fp64)
     pm_deposit<double>(c);
   else
