@@ -40,16 +40,42 @@ __device__ __forceinline__ R frac32(uint32_t lo) {
   return (R)lo * (R)2.3283064365386963e-10;  // 2^-32
 }
 
-// rho[node] = sum over the 8 cells node - o, o in {0,1}^3, of k w; output
-// delta.  One block per 8^3 tile of nodes: the CSR bounds of the 9^3 cells the
-// tile touches are staged in shared memory once (instead of 16 scattered
-// loads per node); each node then sums its 8 cells in a fixed order (cell
-// offset, then particle order), so the mesh is deterministic.
+// W[o][first particle of a cell] = sum over the cell's particles, in order, of
+// k w_o, w_o the CIC weight of the cell's corner node o = (ox, oy, oz): each
+// particle's weights are computed once (not once per node that reads it)
+template <class R>
+__global__ void k_cic_cellw(const int32_t* __restrict__ d_n, int64_t cap, const uint64_t* __restrict__ key, int sh,
+                            const uint32_t* __restrict__ u, const uint32_t* __restrict__ k, int M,
+                            R* __restrict__ W) {
+  const int64_t n = *d_n;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t c = key[i] >> sh;
+    if (i > 0 && (key[i - 1] >> sh) == c) continue;  // not the first of its cell
+    R acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int64_t j = i; j < n && (key[j] >> sh) == c; ++j) {
+      R fx = frac32<R>((uint32_t)((uint64_t)u[j] * (uint64_t)M));
+      R fy = frac32<R>((uint32_t)((uint64_t)u[cap + j] * (uint64_t)M));
+      R fz = frac32<R>((uint32_t)((uint64_t)u[2 * cap + j] * (uint64_t)M));
+      const R kk = (R)k[j];
+#pragma unroll
+      for (int o = 0; o < 8; ++o) {
+        const int ox = (o >> 2) & 1, oy = (o >> 1) & 1, oz = o & 1;
+        acc[o] += kk * ((ox ? fx : (R)1 - fx) * (oy ? fy : (R)1 - fy) * (oz ? fz : (R)1 - fz));
+      }
+    }
+#pragma unroll
+    for (int o = 0; o < 8; ++o) W[o * cap + i] = acc[o];
+  }
+}
+
+// rho[node] = sum over the 8 cells node - o, o in {0,1}^3, of the cell's
+// corner-o weight sum; output delta.  One block per 8^3 tile of nodes: the CSR
+// bounds of the 9^3 cells the tile touches are staged in shared memory once;
+// each node sums its 8 cells in a fixed order, so the mesh is deterministic.
 template <class R>
 __global__ void __launch_bounds__(256) k_cic_gather(const int32_t* __restrict__ start, const int32_t* __restrict__ d_n,
-                                                    int64_t cap, const uint32_t* __restrict__ u,
-                                                    const uint32_t* __restrict__ k, int M, R* __restrict__ delta,
-                                                    R inv_nbar) {
+                                                    int64_t cap, const R* __restrict__ W, int M,
+                                                    R* __restrict__ delta, R inv_nbar) {
   __shared__ int32_t cs[729], ce[729];
   const int T = M >> 3;
   const int tile = blockIdx.x;
@@ -73,43 +99,62 @@ __global__ void __launch_bounds__(256) k_cic_gather(const int32_t* __restrict__ 
     for (int o = 0; o < 8; ++o) {
       int ox = (o >> 2) & 1, oy = (o >> 1) & 1, oz = o & 1;
       int q = (a - ox + 1) * 81 + (b - oy + 1) * 9 + (c - oz + 1);
-      for (int32_t i = cs[q]; i < ce[q]; ++i) {
-        R fx = frac32<R>((uint32_t)((uint64_t)u[i] * (uint64_t)M));
-        R fy = frac32<R>((uint32_t)((uint64_t)u[cap + i] * (uint64_t)M));
-        R fz = frac32<R>((uint32_t)((uint64_t)u[2 * cap + i] * (uint64_t)M));
-        R w = (ox ? fx : (R)1 - fx) * (oy ? fy : (R)1 - fy) * (oz ? fz : (R)1 - fz);
-        acc += (R)k[i] * w;
-      }
+      if (ce[q] > cs[q]) acc += W[o * cap + cs[q]];
     }
     delta[((int64_t)(bx + a) * M + (by + b)) * M + (bz + c)] = acc * inv_nbar - (R)1;
   }
 }
 
-// g = -grad phi (four-point stencil at the 8 surrounding nodes), CIC weights
+// g = -grad phi (four-point stencil at the 8 surrounding nodes), CIC weights.
+// One block per 8^3 tile of cells = one depth-(m-3) octree cell, whose
+// particles are one contiguous Morton run: the block stages the 13^3 nodes of
+// phi the tile's stencils reach, forms the gradient at the 9^3 corner nodes in
+// shared memory (the same four-point formula per node), then interpolates
+// every particle of the tile from shared memory.
 template <class R>
-__global__ void k_pm_interp(const int32_t* __restrict__ d_n, int64_t cap, const uint32_t* __restrict__ u,
-                            const R* __restrict__ phi, int M, R inv12dx, R* __restrict__ g) {
-  const int64_t n = *d_n;
+__global__ void __launch_bounds__(256) k_pm_interp_tile(const int32_t* __restrict__ start, int64_t cap,
+                                                        const uint32_t* __restrict__ u, const R* __restrict__ phi,
+                                                        int M, R inv12dx, R* __restrict__ g) {
+  extern __shared__ unsigned char pi_raw[];
+  R* ph = reinterpret_cast<R*>(pi_raw);  // [13][13][13], node (bx - 2 + i, ...)
+  R* gr = ph + 2197;                     // [3][9][9][9], corner node (bx + i, ...)
+  const int T = M >> 3;
+  const int tile = blockIdx.x;
+  const int tx = tile / (T * T), ty = (tile / T) % T, tz = tile % T;
+  const int bx = tx * 8, by = ty * 8, bz = tz * 8;
+  // the tile's particles: Morton prefix of the tile at depth m - 3
+  const uint32_t tp = (uint32_t)((spread3((uint32_t)tx) << 2) | (spread3((uint32_t)ty) << 1) | spread3((uint32_t)tz));
+  const int32_t p0 = start[(int64_t)tp << 9], p1 = start[((int64_t)tp + 1) << 9];
+  if (p1 <= p0) return;  // empty tile (uniform across the block)
   const int mask = M - 1;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    uint64_t tx = (uint64_t)u[i] * (uint64_t)M, ty = (uint64_t)u[cap + i] * (uint64_t)M,
-             tz = (uint64_t)u[2 * cap + i] * (uint64_t)M;
-    int bx = (int)(tx >> 32), by = (int)(ty >> 32), bz = (int)(tz >> 32);
-    R fx = frac32<R>((uint32_t)tx), fy = frac32<R>((uint32_t)ty), fz = frac32<R>((uint32_t)tz);
+  for (int q = threadIdx.x; q < 2197; q += blockDim.x) {
+    const int i = q / 169, j = (q / 13) % 13, l = q % 13;
+    ph[q] = phi[((int64_t)((bx - 2 + i) & mask) * M + ((by - 2 + j) & mask)) * M + ((bz - 2 + l) & mask)];
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < 729; q += blockDim.x) {
+    const int i = q / 81 + 2, j = (q / 9) % 9 + 2, l = q % 9 + 2;
+    auto P = [&](int x, int y, int z) -> R { return ph[(x * 13 + y) * 13 + z]; };
+    gr[q] = (R)8 * (P(i + 1, j, l) - P(i - 1, j, l)) - (P(i + 2, j, l) - P(i - 2, j, l));
+    gr[729 + q] = (R)8 * (P(i, j + 1, l) - P(i, j - 1, l)) - (P(i, j + 2, l) - P(i, j - 2, l));
+    gr[1458 + q] = (R)8 * (P(i, j, l + 1) - P(i, j, l - 1)) - (P(i, j, l + 2) - P(i, j, l - 2));
+  }
+  __syncthreads();
+  for (int64_t i = p0 + threadIdx.x; i < p1; i += blockDim.x) {
+    uint64_t sx = (uint64_t)u[i] * (uint64_t)M, sy = (uint64_t)u[cap + i] * (uint64_t)M,
+             sz = (uint64_t)u[2 * cap + i] * (uint64_t)M;
+    // 0..7 by construction (the particle lies in the tile); clamped all the same
+    const int cx = min(max((int)(sx >> 32) - bx, 0), 7), cy = min(max((int)(sy >> 32) - by, 0), 7),
+              cz = min(max((int)(sz >> 32) - bz, 0), 7);
+    R fx = frac32<R>((uint32_t)sx), fy = frac32<R>((uint32_t)sy), fz = frac32<R>((uint32_t)sz);
     R ax = 0, ay = 0, az = 0;
     for (int o = 0; o < 8; ++o) {
       int ox = (o >> 2) & 1, oy = (o >> 1) & 1, oz = o & 1;
       R w = (ox ? fx : (R)1 - fx) * (oy ? fy : (R)1 - fy) * (oz ? fz : (R)1 - fz);
-      int a = (bx + ox) & mask, b = (by + oy) & mask, cc = (bz + oz) & mask;
-      auto P = [&](int x, int y, int z) -> R {
-        return phi[((int64_t)(x & mask) * M + (y & mask)) * M + (z & mask)];
-      };
-      R gx = (R)8 * (P(a + 1, b, cc) - P(a - 1, b, cc)) - (P(a + 2, b, cc) - P(a - 2, b, cc));
-      R gy = (R)8 * (P(a, b + 1, cc) - P(a, b - 1, cc)) - (P(a, b + 2, cc) - P(a, b - 2, cc));
-      R gz = (R)8 * (P(a, b, cc + 1) - P(a, b, cc - 1)) - (P(a, b, cc + 2) - P(a, b, cc - 2));
-      ax -= w * gx;
-      ay -= w * gy;
-      az -= w * gz;
+      const int q = ((cx + ox) * 9 + (cy + oy)) * 9 + (cz + oz);
+      ax -= w * gr[q];
+      ay -= w * gr[729 + q];
+      az -= w * gr[1458 + q];
     }
     g[i] = ax * inv12dx;
     g[cap + i] = ay * inv12dx;
@@ -125,7 +170,10 @@ void pm_deposit(dzs_ctx* c) {
   const int64_t m3 = (int64_t)M * M * M;
   double n0 = (double)c->N0;
   R inv_nbar = (R)((double)m3 / n0);
-  k_cic_gather<R><<<(unsigned)(m3 / 512), 256, 0, c->stream>>>(B.cell_start, B.n, c->cap, B.u, B.k, M, (R*)B.rho, inv_nbar);
+  const int sh = 3 * (kMaxLevel - c->logM);
+  k_cic_cellw<R><<<grid_for(c->N0), kThreads, 0, c->stream>>>(B.n, c->cap, B.key, sh, B.u, B.k, M, (R*)B.cicw);
+  k_cic_gather<R><<<(unsigned)(m3 / 512), 256, 0, c->stream>>>(B.cell_start, B.n, c->cap, (const R*)B.cicw, M,
+                                                               (R*)B.rho, inv_nbar);
 }
 
 template <class R>
@@ -144,8 +192,10 @@ void pm_interp(dzs_ctx* c) {
   Buffers& B = c->B;
   const int M = c->M;
   R inv12dx = (R)(1.0 / (12.0 * c->P.box / M));
-  k_pm_interp<R><<<grid_for(c->N0), kThreads, 0, c->stream>>>(B.n, c->cap, B.u, (const R*)B.phi, M, inv12dx,
-                                                              (R*)B.g);
+  const int64_t tiles = (int64_t)(M / 8) * (M / 8) * (M / 8);
+  const size_t sm = (2197 + 3 * 729) * sizeof(R);
+  k_pm_interp_tile<R><<<(unsigned)tiles, 256, sm, c->stream>>>(B.cell_start, c->cap, B.u, (const R*)B.phi, M,
+                                                               inv12dx, (R*)B.g);
 }
 
 // ---- 3D power spectrum of the mesh (forward spectrum of the CIC delta)
@@ -250,8 +300,9 @@ void pk_impl(dzs_ctx* c, int nbins, double* d_part, double* d_out, double shot) 
   const int sh = 3 * (kMaxLevel - c->logM);
   k_cell_start<<<grid_for(c->N0 + 1), kThreads, 0, c->stream>>>(B.n, B.key, sh, m3, B.cell_start);
   R inv_nbar = (R)((double)m3 / (double)c->N0);
-  k_cic_gather<R><<<(unsigned)(m3 / 512), 256, 0, c->stream>>>(B.cell_start, B.n, c->cap, B.u, B.k, M, (R*)B.rho,
-                                                               inv_nbar);
+  k_cic_cellw<R><<<grid_for(c->N0), kThreads, 0, c->stream>>>(B.n, c->cap, B.key, sh, B.u, B.k, M, (R*)B.cicw);
+  k_cic_gather<R><<<(unsigned)(m3 / 512), 256, 0, c->stream>>>(B.cell_start, B.n, c->cap, (const R*)B.cicw, M,
+                                                               (R*)B.rho, inv_nbar);
   fft_r2c_3d<R>(c, (const R*)B.rho, (cplx<R>*)B.spec, M, (const cplx<R>*)B.twiddle);
   const double L = c->P.box;
   const double norm = L * L * L / ((double)m3 * (double)m3);
@@ -267,7 +318,7 @@ void pk_impl(dzs_ctx* c, int nbins, double* d_part, double* d_out, double shot) 
 // [nbins][3]; d_part holds M * nbins * 3 doubles.  The state must be
 // Morton-sorted with valid keys.
 void launch_pk(dzs_ctx* c, int nbins, double* d_part, double* d_out, double shot) {
-  c->launches += c->fp64 ? 7 : 7;
+  c->launches += 8;
   if (c->fp64)
     pk_impl<double>(c, nbins, d_part, d_out, shot);
   else
@@ -292,7 +343,7 @@ void launch_cell_start(dzs_ctx* c) {
 }
 
 void launch_pm_deposit(dzs_ctx* c) {
-  c->launches += 1;
+  c->launches += 2;
   if (c->fp64)
     pm_deposit<double>(c);
   else
