@@ -126,7 +126,7 @@ struct Plan {
     o_cicw = L.take(8 * rsz * cap);
     o_groups = L.take(4 * cap);
     o_ghead = L.take(4 * cap);
-    o_wpm = L.take(rsz * cap);
+    o_wpm = L.take((rsz == 8 ? 24 : 16) * cap);  // packed walk entries: lattice position, G m
     o_wph = L.take(rsz * cap);
     o_wnh = L.take(rsz * node_cap);
     o_rho = L.take(rsz * m3);

@@ -16,6 +16,8 @@
 // (uint64), the rounded integer COM and the largest member multiplicity (node
 // softening).  Walk groups (node with <= G particles whose parent holds more,
 // or a leaf) are listed in Morton order.
+#include <cuda/atomic>
+
 #include "common.cuh"
 
 namespace dzs {
@@ -155,9 +157,10 @@ __global__ void k_tree_up_all(const int32_t* __restrict__ lvl, int64_t cap, cons
       const int32_t par = parent[cur];
       if (par < 0) break;
       const int nch = (int)((nodes[par].meta >> 8) & 0xff);
-      __threadfence();  // this subtree's sums before the arrival
-      if (atomicAdd(&arrive[par], 1) + 1 < nch) break;
-      __threadfence();
+      // release this subtree's sums with the arrival; the last arriver acquires
+      // every sibling's
+      cuda::atomic_ref<int32_t, cuda::thread_scope_device> arr(arrive[par]);
+      if (arr.fetch_add(1, cuda::memory_order_acq_rel) + 1 < nch) break;
       const int32_t c0 = nodes[par].child;
       uint64_t PK = 0, PS[3] = {0, 0, 0};
       uint32_t pkmax = 0;

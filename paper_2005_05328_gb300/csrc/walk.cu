@@ -164,10 +164,12 @@ __device__ __forceinline__ int warp_incl_scan(int v, int lane) {
   return v;
 }
 
-// per-step walk inputs: particle G m / s^2 and spline radius, node spline radius
+// per-step walk inputs: packed particle entries (position, G m / s^2) and spline
+// radius, node spline radius
 template <class R>
-__global__ void k_walk_prep(const int32_t* __restrict__ d_n, const uint32_t* __restrict__ k,
-                            const int32_t* __restrict__ lvl, const Node* __restrict__ nodes, R* __restrict__ pm,
+__global__ void k_walk_prep(const int32_t* __restrict__ d_n, int64_t cap, const uint32_t* __restrict__ u,
+                            const uint32_t* __restrict__ k, const int32_t* __restrict__ lvl,
+                            const Node* __restrict__ nodes, Entry<R>* __restrict__ pm,
                             R* __restrict__ ph, R* __restrict__ nh, R gm0, R h0) {
   const int64_t n = *d_n;
   int64_t nn = 0;
@@ -176,7 +178,12 @@ __global__ void k_walk_prep(const int32_t* __restrict__ d_n, const uint32_t* __r
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
     if (i < n) {
       uint32_t kk = k[i];
-      pm[i] = gm0 * (R)kk;
+      Entry<R> E;  // packed: one vector load per particle the walk lists
+      E.x = u[i];
+      E.y = u[cap + i];
+      E.z = u[2 * cap + i];
+      E.m = gm0 * (R)kk;
+      pm[i] = E;
       ph[i] = kk == 1 ? h0 : h0 * cbrt((R)kk);
     }
     if (i < nn) {
@@ -190,7 +197,7 @@ template <class R>
 __global__ void __launch_bounds__(kWarps * 32) k_walk(
     const int32_t* __restrict__ groups, const uint64_t* __restrict__ counters, unsigned int* __restrict__ next,
     const Node* __restrict__ nodes, const R* __restrict__ nh, int64_t cap, const uint32_t* __restrict__ u,
-    const R* __restrict__ pm, const R* __restrict__ ph, R* __restrict__ p, R* __restrict__ g, WalkConst<R> C,
+    const Entry<R>* __restrict__ pm, const R* __restrict__ ph, R* __restrict__ p, R* __restrict__ g, WalkConst<R> C,
     uint32_t* __restrict__ err, unsigned long long* __restrict__ pairs) {
   extern __shared__ unsigned char smem_raw[];
   WalkSmem<R>& sm = *reinterpret_cast<WalkSmem<R>*>(smem_raw);
@@ -335,11 +342,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(
             int sst = __shfl_sync(0xffffffffu, lstart, src);
             if (t < totl) {
               int64_t j = (int64_t)sst + (t - (send - scnt));
-              Entry<R> E;
-              E.x = u[j];
-              E.y = u[cap + j];
-              E.z = u[2 * cap + j];
-              E.m = pm[j];
+              Entry<R> E = pm[j];
               sm.e[w][len + t] = E;
               sm.h[w][len + t] = ph[j];
             }
@@ -364,11 +367,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(
               int mm = bc - q0 < 32 ? bc - q0 : 32;
               if (lane < mm) {
                 int64_t j = (int64_t)bs + q0 + lane;
-                Entry<R> E;
-                E.x = u[j];
-                E.y = u[cap + j];
-                E.z = u[2 * cap + j];
-                E.m = pm[j];
+                Entry<R> E = pm[j];
                 sm.e[w][len + lane] = E;
                 sm.h[w][len + lane] = ph[j];
               }
@@ -444,11 +443,12 @@ void walk_impl(dzs_ctx* c, bool tree, bool close_kick, int step) {
   C.close = close_kick ? 1 : 0;
   C.tree = tree ? 1 : 0;
   C.poly = (c->P.rcut_rs / 2.0 <= (double)kSplitXMax) ? 1 : 0;
-  R* pm = (R*)c->B.wpm;
+  Entry<R>* pm = (Entry<R>*)c->B.wpm;
   R* ph = (R*)c->B.wph;
   R* nh = (R*)c->B.wnh;
-  k_walk_prep<R><<<grid_for(c->node_cap), kThreads, 0, c->stream>>>(c->B.n, c->B.k, c->B.lvl_count, c->B.nodes, pm,
-                                                                     ph, nh, C.gm0, (R)(2.8 * c->eps0 / s));
+  k_walk_prep<R><<<grid_for(c->node_cap), kThreads, 0, c->stream>>>(c->B.n, c->cap, c->B.u, c->B.k, c->B.lvl_count,
+                                                                     c->B.nodes, pm, ph, nh, C.gm0,
+                                                                     (R)(2.8 * c->eps0 / s));
   size_t sm = sizeof(WalkSmem<R>);
   static bool attr_done[2] = {false, false};
   if (!attr_done[sizeof(R) == 8]) {
