@@ -108,6 +108,8 @@ def _declare(L):
         "dzso_skymap": (None, [P, i64, vp, i64, d, d, vp]),
         "dzso_pix2zphi_ring_many": (None, [i64, i64, vp, vp, vp]),
         "dzso_lcdensity": (None, [P, i64, vp, i64, d, d, vp]),
+        "dzso_fof_threshold": (u64, [P, d]),
+        "dzso_fof": (i64, [P, i64, vp, vp, d, i32, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -396,3 +398,23 @@ def lcdensity(P, rec, mesh, a_lo=0.0, a_hi=2.0):
     lib().dzso_lcdensity(byref(P), len(rec), rec.ctypes.data_as(C.c_void_p), int(mesh), float(a_lo),
                          float(a_hi), _ptr(g))
     return g.reshape(mesh, mesh, mesh)
+
+
+# ---------------- friends-of-friends ----------------
+
+HALO_DTYPE = np.dtype([("first", "<i8"), ("count", "<i8"), ("mass", "<u8"), ("x", "<f8", (3,)),
+                       ("rmax2", "<u8")])
+
+
+def fof_threshold(P, link): return lib().dzso_fof_threshold(byref(P), float(link))
+
+
+def fof(P, u, k, link=0.2, nmin=20):
+    """-> (haloes [HALO_DTYPE], label per particle: first member or -1)"""
+    u = _c(u, np.uint32); k = _c(k, np.uint32)
+    n = u.shape[1]
+    lab = np.zeros(n, np.int64)
+    h = np.zeros(max(n, 1), HALO_DTYPE)
+    nh = lib().dzso_fof(byref(P), n, _ptr(u), _ptr(k), float(link), int(nmin), _ptr(lab),
+                        h.ctypes.data_as(C.c_void_p))
+    return h[:nh].copy(), lab

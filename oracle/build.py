@@ -8,7 +8,7 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SOURCES = ["cosmo.c", "fft.c", "ics.c", "pm.c", "tree.c", "merge.c", "step.c", "observe.c"]
+SOURCES = ["cosmo.c", "fft.c", "ics.c", "pm.c", "tree.c", "merge.c", "step.c", "observe.c", "fof.c"]
 LIB = os.path.join(HERE, "liboracle.so")
 
 

@@ -177,4 +177,20 @@ void dzso_lcdensity(const dzso_params* P, int64_t nrec, const dzso_record* rec, 
                     double a_hi, uint64_t* grid);
 void dzso_pix2zphi_ring_many(int64_t nside, int64_t n, const int64_t* pix, double* z, double* phi);
 
+/* ---- friends-of-friends haloes (fof.c) ---- */
+typedef struct {
+  int64_t first;   /* smallest member index (labels the halo) */
+  int64_t count;   /* particles */
+  uint64_t mass;   /* sum k */
+  double x[3];     /* centre of mass, Mpc/h, wrapped into [0, L) */
+  uint64_t rmax2;  /* largest squared lattice distance of a member from the observer */
+} dzso_halo;
+/* linking threshold on the squared lattice distance: floor((link 2^32 / n1d)^2) */
+uint64_t dzso_fof_threshold(const dzso_params* P, double link);
+/* haloes (components with >= nmin particles) of the set u[3][n], masses k;
+ * label[i] (may be NULL) = first member of i's halo or -1; returns the halo
+ * count, haloes in increasing first-member order (halos sized >= n) */
+int64_t dzso_fof(const dzso_params* P, int64_t n, const uint32_t* u, const uint32_t* k, double link, int32_t nmin,
+                 int64_t* label, dzso_halo* halos);
+
 #endif
