@@ -334,6 +334,33 @@ typedef struct {
 DZS_API dzs_status dzs_serve(const dzs_serve_config* cfg, const dzs_request* req, size_t n,
                              dzs_request_result* out, double* wall_s);
 
+/* Friends-of-friends haloes of the current particles (Sec. 3.1.1: the
+ * lightcone halo mass function is built from FoF catalogues of frequent
+ * outputs, keeping the haloes entirely inside the lightcone).  Two particles
+ * are friends when their minimum-image lattice distance satisfies d^2 <=
+ * floor((link 2^32 / n1d)^2), i.e. d <= link lambda, lambda = L / n1d (link
+ * 0.2 is the usual choice); a halo is a connected component with >= nmin
+ * particles.  Per halo: first = the smallest member index in the current
+ * particle order (it labels the halo), count, mass = sum k (units of m0), the
+ * centre of mass x = (u_first + S / K) L / 2^32 wrapped into [0, L) with S the
+ * exact sum of k times the minimum-image lattice offsets from the first member
+ * and K = mass, and rmax2 = the largest squared lattice distance of a member
+ * from the observer (a halo is entirely inside the lightcone when rmax2 <
+ * R_lat^2).  Haloes in increasing `first`; *nhalo = their number (only the
+ * first `cap` are copied); label (may be NULL, n entries) = each particle's
+ * halo `first` or -1.  Needs nmin >= 2 and 0 < link lambda < L / 4;
+ * deterministic (the components are unique, every
+ * sum is an integer sum).  The state is unchanged.  Synchronises. */
+typedef struct {
+  int64_t first;
+  int64_t count;
+  uint64_t mass;
+  double x[3];
+  uint64_t rmax2;
+} dzs_halo;
+DZS_API dzs_status dzs_fof(dzs_ctx* c, double link, int32_t nmin, dzs_halo* halos, size_t cap, size_t* nhalo,
+                           int64_t* label);
+
 DZS_API dzs_status dzs_get_tables(dzs_ctx* c, double* a, double* drift, double* kick1, double* kick2,
                           double* rlc, uint64_t* rlat);
 

@@ -36,7 +36,7 @@ EXPORTED = ["dzs_params_default", "dzs_footprint_bytes", "dzs_create", "dzs_ics"
             "dzs_get_mesh", "dzs_get_counters", "dzs_set_profiling", "dzs_get_profile",
             "dzs_morton_sort_noalloc", "dzs_checkpoint_bytes", "dzs_checkpoint", "dzs_restore",
             "dzs_step_until", "dzs_observe_enable", "dzs_observe_add_records", "dzs_skymap_get",
-            "dzs_lcdensity_get", "dzs_skymap_alm", "dzs_power_spectrum", "dzs_serve", "dzs_last_error"]
+            "dzs_lcdensity_get", "dzs_skymap_alm", "dzs_power_spectrum", "dzs_serve", "dzs_fof", "dzs_last_error"]
 NOALLOC_SORT_MAX_N = 262144
 PROF_NAMES = ["kick_drift", "sort", "merge", "tree", "pm", "walk", "fft"]
 
@@ -83,6 +83,9 @@ class Observe(C.Structure):
     _fields_ = [("nside", C.c_int32), ("mesh", C.c_int32), ("a_lo", C.c_double), ("a_hi", C.c_double)]
 
 
+HALO_DTYPE = np.dtype([("first", "<i8"), ("count", "<i8"), ("mass", "<u8"), ("x", "<f8", (3,)),
+                       ("rmax2", "<u8")])
+
 RECORD_DTYPE = np.dtype([("id", "<u4"), ("k", "<u4"), ("a_cross", "<f8"),
                          ("x", "<f8", (3,)), ("p", "<f8", (3,))])
 
@@ -124,6 +127,7 @@ def load(path: str = LIB_PATH):
         "dzs_skymap_get": [vp, vp, sz], "dzs_lcdensity_get": [vp, vp, sz],
         "dzs_skymap_alm": [vp, i32, vp, vp], "dzs_power_spectrum": [vp, i32, i32, vp, vp, vp],
         "dzs_serve": [C.POINTER(ServeConfig), vp, sz, vp, C.POINTER(C.c_double)],
+        "dzs_fof": [vp, C.c_double, i32, vp, sz, C.POINTER(sz), vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -358,6 +362,19 @@ def dzs_serve(requests, hbm_budget_bytes, max_active=0, steps_per_slice=8, **bas
     return st, wall.value, out
 
 
+def dzs_fof(h, link=0.2, nmin=20, labels=False):
+    """-> haloes [HALO_DTYPE] (and per-particle labels when asked)"""
+    nh = C.c_size_t(0)
+    _check(load().dzs_fof(h, float(link), int(nmin), None, 0, C.byref(nh), None), h)
+    n, _ = dzs_get_count(h)
+    out = np.zeros(max(1, nh.value), HALO_DTYPE)
+    lab = np.zeros(max(1, n), np.int64) if labels else None
+    _check(load().dzs_fof(h, float(link), int(nmin), out.ctypes.data_as(C.c_void_p), nh.value, C.byref(nh),
+                          _ptr(lab)), h)
+    out = out[:nh.value]
+    return (out, lab[:n]) if labels else out
+
+
 def dzs_step_until(h, max_steps: int, ratio_min=0.0, wall_limit_s=0.0, horizon_s=0.0):
     """-> (steps done, DZS_HALT_* reason, last N / N0)"""
     hp = Halt(ratio_min, wall_limit_s, horizon_s)
@@ -414,3 +431,4 @@ class Context:
     def lcdensity(self, mesh): return dzs_lcdensity_get(self.h, mesh)
     def skymap_alm(self, lmax): return dzs_skymap_alm(self.h, lmax)
     def power_spectrum(self, nbins, shot=True): return dzs_power_spectrum(self.h, nbins, shot)
+    def fof(self, link=0.2, nmin=20, labels=False): return dzs_fof(self.h, link, nmin, labels)

@@ -3,6 +3,7 @@
 // diagnostics.  Step order (paper Sec. 2.2: DZS on global steps, tree rebuilt
 // and forces recomputed after a merge): opening kick + drift + crossing ->
 // records -> Morton sort -> merge -> tree -> PM -> walk + closing kick.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -980,6 +981,43 @@ dzs_status dzs_power_spectrum(dzs_ctx* c, int32_t nbins, int32_t flags, double* 
     if (k) k[b] = cnt > 0 ? h[3 * b + 1] / cnt : 0.0;
     pk[b] = cnt > 0 ? h[3 * b + 2] / cnt : 0.0;
   }
+  return check_device_errors(c);
+}
+
+dzs_status dzs_fof(dzs_ctx* c, double link, int32_t nmin, dzs_halo* halos, size_t cap, size_t* nhalo,
+                   int64_t* label) {
+  dzs_status s = guard(c);
+  if (s) return s;
+  if (!c->have_state) return fail(c, DZS_ESTATE, "no particle state");
+  if (!(link > 0) || !(link * c->P.box / c->P.n1d < 0.25 * c->P.box) || nmin < 2 || !nhalo || (cap && !halos))
+    return fail(c, DZS_EINVAL, "need 0 < link lambda < L / 4, nmin >= 2, nhalo");
+  // friends: d^2 <= floor((link 2^32 / n1d)^2) (FP64, then integer)
+  const double lb = link * 4294967296.0 / (double)c->P.n1d;
+  const uint64_t T = (uint64_t)std::floor(lb * lb);
+  // the finest cell depth <= log2 M whose side exceeds the linking length
+  int depth = c->logM;
+  while (depth > 1 && std::ldexp(1.0, 32 - depth) * std::ldexp(1.0, 32 - depth) < (double)T + 1.0) --depth;
+  // work on the Morton order, then put the state back in its order
+  launch_keys(c);
+  launch_sort(c);
+  dzs_halo* d_h = nullptr;
+  int64_t* d_label = label ? (int64_t*)c->B.key2 : nullptr;
+  launch_fof(c, depth, T, nmin, d_label, &d_h);
+  int32_t nh = 0;
+  CK(cudaMemcpyAsync(&nh, c->B.n + 2, sizeof nh, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  s = check_device_errors(c);
+  if (s) return s;
+  std::vector<dzs_halo> h((size_t)nh);
+  if (nh) CK(cudaMemcpy(h.data(), d_h, sizeof(dzs_halo) * (size_t)nh, cudaMemcpyDeviceToHost));
+  size_t n = 0;
+  CK(cudaMemcpy(&n, c->B.n, sizeof(int32_t), cudaMemcpyDeviceToHost));
+  if (label) CK(cudaMemcpy(label, d_label, sizeof(int64_t) * (size_t)(int32_t)n, cudaMemcpyDeviceToHost));
+  launch_unpermute(c, (double*)c->B.convert);
+  CK(cudaGetLastError());
+  std::sort(h.begin(), h.end(), [](const dzs_halo& a, const dzs_halo& b) { return a.first < b.first; });
+  *nhalo = (size_t)nh;
+  for (size_t i = 0; i < h.size() && i < cap; ++i) halos[i] = h[i];
   return check_device_errors(c);
 }
 

@@ -220,6 +220,7 @@ void launch_to_double(dzs_ctx* c, const void* src, int64_t count, double* dst);
 void launch_from_double(dzs_ctx* c, const double* src, int64_t count, void* dst);
 void launch_fft_init(dzs_ctx* c);
 void launch_pk(dzs_ctx* c, int nbins, double* d_part, double* d_out, double shot);
+void launch_fof(dzs_ctx* c, int depth, uint64_t T, int nmin, int64_t* d_label, dzs_halo** d_halos);
 void launch_sum_k2(dzs_ctx* c, unsigned long long* out);
 void launch_observe_records(dzs_ctx* c, const dzs_lc_record* d_rec, int64_t n);
 size_t sht_work_bytes(int64_t nside, int lmax);

@@ -93,6 +93,8 @@ def test_struct_layouts_match_the_header(tmp_path, dzs):
     body += ['  printf("%%zu\\n", offsetof(dzs_observe, %s));' % f for f in obs]
     extra = [("dzs_request", dzs.Request), ("dzs_request_result", dzs.RequestResult),
              ("dzs_serve_config", dzs.ServeConfig)]
+    body += ['  printf("%zu\\n", sizeof(dzs_halo));']
+    body += ['  printf("%%zu\\n", offsetof(dzs_halo, %s));' % f for f in dzs.HALO_DTYPE.names]
     for cname, cls in extra:
         body += ['  printf("%%zu\\n", sizeof(%s));' % cname]
         body += ['  printf("%%zu\\n", offsetof(%s, %s));' % (cname, f[0]) for f in cls._fields_]
@@ -105,6 +107,7 @@ def test_struct_layouts_match_the_header(tmp_path, dzs):
     want = [ctypes.sizeof(dzs.Params)] + [getattr(dzs.Params, f).offset for f in fields]
     want += [ctypes.sizeof(dzs.Halt)] + [getattr(dzs.Halt, f).offset for f in halt]
     want += [ctypes.sizeof(dzs.Observe)] + [getattr(dzs.Observe, f).offset for f in obs]
+    want += [dzs.HALO_DTYPE.itemsize] + [dzs.HALO_DTYPE.fields[f][1] for f in dzs.HALO_DTYPE.names]
     for cname, cls in extra:
         want += [ctypes.sizeof(cls)] + [getattr(cls, f[0]).offset for f in cls._fields_]
     want += [dzs.RECORD_DTYPE.itemsize]
