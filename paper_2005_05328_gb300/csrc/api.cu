@@ -30,8 +30,10 @@ int ilog2i(int64_t v) {
 
 const char* validate(const dzs_params* p) {
   if (!p) return "params is NULL";
-  if (!is_pow2(p->n1d) || p->n1d < 2 || p->n1d > 512) return "n1d must be a power of two in [2, 512]";
-  if (!is_pow2(p->mesh) || p->mesh < 8 || p->mesh > 512) return "mesh must be a power of two in [8, 512]";
+  auto pow2_or_3pow2 = [](int64_t v) { return is_pow2(v) || (v % 3 == 0 && is_pow2(v / 3)); };
+  if (!pow2_or_3pow2(p->n1d) || p->n1d < 2 || p->n1d > 512) return "n1d must be 2^a or 3 2^a in [2, 512]";
+  if (!pow2_or_3pow2(p->mesh) || p->mesh < 8 || p->mesh > 512 || p->mesh % 8 != 0)
+    return "mesh must be 2^a or 3 2^a, a multiple of 8, in [8, 512]";
   if (!(p->box > 0)) return "box must be positive";
   if (!(p->omega_m > 0) || !(p->omega_l >= 0)) return "omega_m > 0 and omega_l >= 0 required";
   if (!(p->hubble > 0) || !(p->sigma8 >= 0)) return "hubble > 0 and sigma8 >= 0 required";
@@ -316,7 +318,8 @@ dzs_status dzs_create(const dzs_params* p, void* cuda_stream, dzs_ctx** out) {
   c->N0 = (int64_t)p->n1d * p->n1d * p->n1d;
   c->cap = p->capacity ? (int64_t)p->capacity : c->N0;
   c->M = p->mesh;
-  c->logM = ilog2i(p->mesh);
+  c->mesh_pow2 = is_pow2(p->mesh);
+  c->logM = ilog2i(p->mesh) - (c->mesh_pow2 ? 0 : 1);  // floor(log2 M): depth of the Morton cell table
   c->lat = 4294967296.0 / p->box;
   c->scale = p->box / 4294967296.0;
   c->gm0 = 1.5 * p->omega_m * p->box * p->box * p->box / (4.0 * M_PI * (double)c->N0);

@@ -153,7 +153,8 @@ struct dzs_ctx {
   cudaStream_t stream = nullptr;
   bool fp64 = false;
   int64_t N0 = 0, cap = 0, node_cap = 0;
-  int M = 0, logM = 0, n1 = 0;
+  int M = 0, logM = 0, n1 = 0;  // logM: depth of the Morton cell table (floor log2 M)
+  bool mesh_pow2 = true;         // false: M = 3 2^a, deposited through a row-major cell sort
   int sort_blocks = 0;
   double lat = 0, scale = 0, gm0 = 0, eps0 = 0, rs = 0, rcut = 0, rcut_lat2 = 0;
   int jmin = 1;
@@ -203,6 +204,7 @@ double bbks_shape(const dzs_params& P, double k);  // k^ns T(k)^2
 void launch_kick_drift(dzs_ctx* c, int step, bool kick, bool drift);
 void launch_records(dzs_ctx* c, int step);
 void launch_sort(dzs_ctx* c);
+void launch_sort_keys(dzs_ctx* c, uint64_t* ka, uint64_t* kb, uint32_t* va, uint32_t* vb, int passes);
 void launch_keys(dzs_ctx* c);
 void launch_unpermute(dzs_ctx* c, double* g_out);
 void launch_close_kick(dzs_ctx* c, int step);

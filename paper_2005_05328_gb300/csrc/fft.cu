@@ -9,8 +9,10 @@
 //   X      -- same along ix; for the Poisson solve the forward FFT, the Green
 //             multiply and the inverse FFT are fused in one pass;
 //   Y inverse, Z c2r.
-// Each length-n transform is a four-step FFT, n = N1 N2 (N1 >= N2, powers of
-// two): N2 register FFTs of length N1 (input stride N2), twiddle W_n^(j2 k1),
+// Each length-n transform is a four-step FFT, n = N1 N2 (n = 2^a, or 3 2^a
+// with the factor 3 in N1; N2 a power of two): N2 register FFTs of length N1
+// (input stride N2; a length 3 M register FFT is three length-M FFTs and
+// radix-3 butterflies), twiddle W_n^(j2 k1),
 // one exchange through shared memory, N1 register FFTs of length N2.  A thread
 // owns one length-N1 and one length-N2 sub-transform of one column, so a
 // column costs two register FFTs and one shared-memory round trip instead of
@@ -26,9 +28,13 @@ namespace {
 
 __constant__ cplx<float> kTw32f[32];   // exp(-2 pi i t / 32)
 __constant__ cplx<double> kTw32d[32];
+__constant__ cplx<float> kTw48f[48];   // exp(-2 pi i t / 48) (register FFTs of length 3 2^a <= 48)
+__constant__ cplx<double> kTw48d[48];
 
 __device__ __forceinline__ cplx<float> tw32(int t, float) { return kTw32f[t]; }
 __device__ __forceinline__ cplx<double> tw32(int t, double) { return kTw32d[t]; }
+__device__ __forceinline__ cplx<float> tw48(int t, float) { return kTw48f[t]; }
+__device__ __forceinline__ cplx<double> tw48(int t, double) { return kTw48d[t]; }
 
 constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n >> 1); }
 constexpr int brevc(int v, int bits) {
@@ -37,10 +43,54 @@ constexpr int brevc(int v, int bits) {
   return r;
 }
 
-// in-register radix-2 DIT FFT of length K (natural order in and out);
-// inv selects the conjugate twiddles
+template <class R, int K>
+__device__ __forceinline__ void reg_fft(cplx<R> (&a)[K], bool inv);
+
+// length K = 3 M: three length-M FFTs of the residues mod 3, twiddles W_K^(r k),
+// then for each k the radix-3 butterfly with w = exp(-+2 pi i / 3) = c + i s:
+// X[k] = x0 + x1 + x2, X[k + M] = x0 + c (x1 + x2) + i s (x1 - x2),
+// X[k + 2M] = x0 + c (x1 + x2) - i s (x1 - x2)
+template <class R, int K>
+__device__ __forceinline__ void reg_fft3(cplx<R> (&a)[K], bool inv) {
+  constexpr int M = K / 3;
+  cplx<R> s0[M], s1[M], s2[M];
+#pragma unroll
+  for (int j = 0; j < M; ++j) {
+    s0[j] = a[3 * j];
+    s1[j] = a[3 * j + 1];
+    s2[j] = a[3 * j + 2];
+  }
+  if (M > 1) {
+    reg_fft<R, M>(s0, inv);
+    reg_fft<R, M>(s1, inv);
+    reg_fft<R, M>(s2, inv);
+  }
+  const R c = (R)-0.5;
+  const R sn = inv ? (R)0.8660254037844386 : (R)-0.8660254037844386;
+#pragma unroll
+  for (int k = 0; k < M; ++k) {
+    cplx<R> w1 = tw48(k * (48 / K), R(0)), w2 = tw48((2 * k * (48 / K)) % 48, R(0));
+    if (inv) {
+      w1.y = -w1.y;
+      w2.y = -w2.y;
+    }
+    const cplx<R> x0 = s0[k], x1 = cmul(s1[k], w1), x2 = cmul(s2[k], w2);
+    const cplx<R> t1 = {x1.x + x2.x, x1.y + x2.y}, t2 = {x1.x - x2.x, x1.y - x2.y};
+    const cplx<R> m = {x0.x + c * t1.x, x0.y + c * t1.y};
+    a[k] = {x0.x + t1.x, x0.y + t1.y};
+    a[k + M] = {m.x - sn * t2.y, m.y + sn * t2.x};
+    a[k + 2 * M] = {m.x + sn * t2.y, m.y - sn * t2.x};
+  }
+}
+
+// in-register FFT of length K (natural order in and out): radix-2 DIT for a
+// power of two, reg_fft3 for 3 2^a; inv selects the conjugate twiddles
 template <class R, int K>
 __device__ __forceinline__ void reg_fft(cplx<R> (&a)[K], bool inv) {
+  if constexpr (K % 3 == 0) {
+    reg_fft3<R, K>(a, inv);
+    return;
+  }
   constexpr int L = ilog2c(K);
 #pragma unroll
   for (int i = 0; i < K; ++i) {
@@ -70,7 +120,7 @@ __device__ __forceinline__ void reg_fft(cplx<R> (&a)[K], bool inv) {
 // W_n^t from the half table tw[t] = exp(-2 pi i t / n), t < n / 2
 template <class R>
 __device__ __forceinline__ cplx<R> twn(const cplx<R>* __restrict__ tw, int t, int n, bool inv) {
-  t &= n - 1;
+  t %= n;  // n is a compile-time constant at every call (a mask for powers of two)
   cplx<R> w = t < n / 2 ? tw[t] : cplx<R>{-tw[t - n / 2].x, -tw[t - n / 2].y};
   if (inv) w.y = -w.y;
   return w;
@@ -78,8 +128,9 @@ __device__ __forceinline__ cplx<R> twn(const cplx<R>* __restrict__ tw, int t, in
 
 template <int N>
 struct Split {
-  static constexpr int N1 = 1 << ((ilog2c(N) + 1) / 2);
-  static constexpr int N2 = N / N1;
+  // powers of two: N1 = 2^ceil(a/2); N = 3 2^a: N2 = 2^floor(a/2), N1 = N / N2
+  static constexpr int N2 = (N % 3 == 0) ? (1 << (ilog2c(N / 3) / 2)) : N / (1 << ((ilog2c(N) + 1) / 2));
+  static constexpr int N1 = N / N2;
 };
 
 // ---- generic four-step pieces on one column held in shared memory
@@ -316,6 +367,12 @@ void dispatch_r2c(dzs_ctx* c, const R* in, cplx<R>* out, int n, const cplx<R>* t
     case 128: launch_r2c_zy<R, 128>(c, in, out, tw, do_x); break;
     case 256: launch_r2c_zy<R, 256>(c, in, out, tw, do_x); break;
     case 512: launch_r2c_zy<R, 512>(c, in, out, tw, do_x); break;
+    case 12: launch_r2c_zy<R, 12>(c, in, out, tw, do_x); break;
+    case 24: launch_r2c_zy<R, 24>(c, in, out, tw, do_x); break;
+    case 48: launch_r2c_zy<R, 48>(c, in, out, tw, do_x); break;
+    case 96: launch_r2c_zy<R, 96>(c, in, out, tw, do_x); break;
+    case 192: launch_r2c_zy<R, 192>(c, in, out, tw, do_x); break;
+    case 384: launch_r2c_zy<R, 384>(c, in, out, tw, do_x); break;
     default: break;  // sizes are validated at context creation
   }
 }
@@ -330,6 +387,12 @@ void dispatch_c2r(dzs_ctx* c, cplx<R>* in, R* out, int n, const cplx<R>* tw, con
     case 128: launch_c2r<R, 128>(c, in, out, tw, green, gfac); break;
     case 256: launch_c2r<R, 256>(c, in, out, tw, green, gfac); break;
     case 512: launch_c2r<R, 512>(c, in, out, tw, green, gfac); break;
+    case 12: launch_c2r<R, 12>(c, in, out, tw, green, gfac); break;
+    case 24: launch_c2r<R, 24>(c, in, out, tw, green, gfac); break;
+    case 48: launch_c2r<R, 48>(c, in, out, tw, green, gfac); break;
+    case 96: launch_c2r<R, 96>(c, in, out, tw, green, gfac); break;
+    case 192: launch_c2r<R, 192>(c, in, out, tw, green, gfac); break;
+    case 384: launch_c2r<R, 384>(c, in, out, tw, green, gfac); break;
     default: break;
   }
 }
@@ -376,7 +439,7 @@ std::vector<cplx<R>> twiddles(int n) {
 template std::vector<cplx<float>> twiddles<float>(int);
 template std::vector<cplx<double>> twiddles<double>(int);
 
-// the length-32 register-FFT table in constant memory (both precisions)
+// the length-32 and length-48 register-FFT tables in constant memory (both precisions)
 void upload_fft_constants(int dev) {
   static bool done[256] = {false};
   if (dev < 0 || dev >= 256 || done[dev]) return;
@@ -389,6 +452,15 @@ void upload_fft_constants(int dev) {
   }
   cudaMemcpyToSymbol(kTw32f, tf, sizeof tf);
   cudaMemcpyToSymbol(kTw32d, td, sizeof td);
+  cplx<float> tf48[48];
+  cplx<double> td48[48];
+  for (int t = 0; t < 48; ++t) {
+    double ang = -2.0 * M_PI * (double)t / 48.0;
+    td48[t] = {std::cos(ang), std::sin(ang)};
+    tf48[t] = {(float)td48[t].x, (float)td48[t].y};
+  }
+  cudaMemcpyToSymbol(kTw48f, tf48, sizeof tf48);
+  cudaMemcpyToSymbol(kTw48d, td48, sizeof td48);
   done[dev] = true;
 }
 

@@ -68,13 +68,52 @@ __global__ void k_cic_cellw(const int32_t* __restrict__ d_n, int64_t cap, const 
   }
 }
 
+// the same for a mesh of M = 3 2^a: particles visited in row-major cell order
+// through the cell sort (sorted cell keys ck, original indices perm); W is
+// indexed by the sorted position of a cell's first particle
+template <class R>
+__global__ void k_cic_cellw_perm(const int32_t* __restrict__ d_n, int64_t cap, const uint64_t* __restrict__ ck,
+                                 const uint32_t* __restrict__ perm, const uint32_t* __restrict__ u,
+                                 const uint32_t* __restrict__ k, int M, R* __restrict__ W) {
+  const int64_t n = *d_n;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t c = ck[t];
+    if (t > 0 && ck[t - 1] == c) continue;
+    R acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int64_t s = t; s < n && ck[s] == c; ++s) {
+      const int64_t j = perm[s];
+      R fx = frac32<R>((uint32_t)((uint64_t)u[j] * (uint64_t)M));
+      R fy = frac32<R>((uint32_t)((uint64_t)u[cap + j] * (uint64_t)M));
+      R fz = frac32<R>((uint32_t)((uint64_t)u[2 * cap + j] * (uint64_t)M));
+      const R kk = (R)k[j];
+#pragma unroll
+      for (int o = 0; o < 8; ++o) {
+        const int ox = (o >> 2) & 1, oy = (o >> 1) & 1, oz = o & 1;
+        acc[o] += kk * ((ox ? fx : (R)1 - fx) * (oy ? fy : (R)1 - fy) * (oz ? fz : (R)1 - fz));
+      }
+    }
+#pragma unroll
+    for (int o = 0; o < 8; ++o) W[o * cap + t] = acc[o];
+  }
+}
+
+__global__ void k_mesh_keys(const int32_t* __restrict__ d_n, int64_t cap, const uint32_t* __restrict__ u, int M,
+                            uint64_t* __restrict__ ck) {
+  const int64_t n = *d_n;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t cx = ((uint64_t)u[i] * (uint64_t)M) >> 32, cy = ((uint64_t)u[cap + i] * (uint64_t)M) >> 32,
+                   cz = ((uint64_t)u[2 * cap + i] * (uint64_t)M) >> 32;
+    ck[i] = (cx * (uint64_t)M + cy) * (uint64_t)M + cz;
+  }
+}
+
 // rho[node] = sum over the 8 cells node - o, o in {0,1}^3, of the cell's
 // corner-o weight sum; output delta.  One block per 8^3 tile of nodes: the CSR
 // bounds of the 9^3 cells the tile touches are staged in shared memory once;
 // each node sums its 8 cells in a fixed order, so the mesh is deterministic.
 template <class R>
 __global__ void __launch_bounds__(256) k_cic_gather(const int32_t* __restrict__ start, const int32_t* __restrict__ d_n,
-                                                    int64_t cap, const R* __restrict__ W, int M,
+                                                    int64_t cap, const R* __restrict__ W, int M, int rowmajor,
                                                     R* __restrict__ delta, R inv_nbar) {
   __shared__ int32_t cs[729], ce[729];
   const int T = M >> 3;
@@ -84,8 +123,9 @@ __global__ void __launch_bounds__(256) k_cic_gather(const int32_t* __restrict__ 
   const int mask = M - 1;
   for (int q = threadIdx.x; q < 729; q += blockDim.x) {
     int i = q / 81, j = (q / 9) % 9, l = q % 9;
-    uint32_t mc = morton_cell((uint32_t)((bx + i - 1) & mask), (uint32_t)((by + j - 1) & mask),
-                              (uint32_t)((bz + l - 1) & mask));
+    const uint32_t gx = (uint32_t)((bx + i - 1 + M) % M), gy = (uint32_t)((by + j - 1 + M) % M),
+                   gz = (uint32_t)((bz + l - 1 + M) % M);
+    const int64_t mc = rowmajor ? ((int64_t)gx * M + gy) * M + gz : (int64_t)morton_cell(gx, gy, gz);
     int32_t s = start[mc], e = start[mc + 1];
     s = s < 0 ? 0 : s;  // defensive: the table is consistent for sorted keys
     e = e > n ? n : e;
@@ -102,6 +142,38 @@ __global__ void __launch_bounds__(256) k_cic_gather(const int32_t* __restrict__ 
       if (ce[q] > cs[q]) acc += W[o * cap + cs[q]];
     }
     delta[((int64_t)(bx + a) * M + (by + b)) * M + (bz + c)] = acc * inv_nbar - (R)1;
+  }
+}
+
+// g = -grad phi at the particles for any mesh (used for M = 3 2^a): the
+// four-point stencil at the 8 surrounding nodes, CIC weights, from global memory
+template <class R>
+__global__ void k_pm_interp(const int32_t* __restrict__ d_n, int64_t cap, const uint32_t* __restrict__ u,
+                            const R* __restrict__ phi, int M, R inv12dx, R* __restrict__ g) {
+  const int64_t n = *d_n;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t tx = (uint64_t)u[i] * (uint64_t)M, ty = (uint64_t)u[cap + i] * (uint64_t)M,
+             tz = (uint64_t)u[2 * cap + i] * (uint64_t)M;
+    int bx = (int)(tx >> 32), by = (int)(ty >> 32), bz = (int)(tz >> 32);
+    R fx = frac32<R>((uint32_t)tx), fy = frac32<R>((uint32_t)ty), fz = frac32<R>((uint32_t)tz);
+    R ax = 0, ay = 0, az = 0;
+    auto P = [&](int x, int y, int z) -> R {
+      return phi[((int64_t)((x + M) % M) * M + ((y + M) % M)) * M + ((z + M) % M)];
+    };
+    for (int o = 0; o < 8; ++o) {
+      int ox = (o >> 2) & 1, oy = (o >> 1) & 1, oz = o & 1;
+      R w = (ox ? fx : (R)1 - fx) * (oy ? fy : (R)1 - fy) * (oz ? fz : (R)1 - fz);
+      int a = (bx + ox) % M, b = (by + oy) % M, cc = (bz + oz) % M;
+      R gx = (R)8 * (P(a + 1, b, cc) - P(a - 1, b, cc)) - (P(a + 2, b, cc) - P(a - 2, b, cc));
+      R gy = (R)8 * (P(a, b + 1, cc) - P(a, b - 1, cc)) - (P(a, b + 2, cc) - P(a, b - 2, cc));
+      R gz = (R)8 * (P(a, b, cc + 1) - P(a, b, cc - 1)) - (P(a, b, cc + 2) - P(a, b, cc - 2));
+      ax -= w * gx;
+      ay -= w * gy;
+      az -= w * gz;
+    }
+    g[i] = ax * inv12dx;
+    g[cap + i] = ay * inv12dx;
+    g[2 * cap + i] = az * inv12dx;
   }
 }
 
@@ -170,9 +242,25 @@ void pm_deposit(dzs_ctx* c) {
   const int64_t m3 = (int64_t)M * M * M;
   double n0 = (double)c->N0;
   R inv_nbar = (R)((double)m3 / n0);
-  const int sh = 3 * (kMaxLevel - c->logM);
-  k_cic_cellw<R><<<grid_for(c->N0), kThreads, 0, c->stream>>>(B.n, c->cap, B.key, sh, B.u, B.k, M, (R*)B.cicw);
-  k_cic_gather<R><<<(unsigned)(m3 / 512), 256, 0, c->stream>>>(B.cell_start, B.n, c->cap, (const R*)B.cicw, M,
+  if (c->mesh_pow2) {
+    // mesh cells are the depth-m Morton cells of the tree's table
+    const int sh = 3 * (kMaxLevel - c->logM);
+    k_cic_cellw<R><<<grid_for(c->N0), kThreads, 0, c->stream>>>(B.n, c->cap, B.key, sh, B.u, B.k, M, (R*)B.cicw);
+    k_cic_gather<R><<<(unsigned)(m3 / 512), 256, 0, c->stream>>>(B.cell_start, B.n, c->cap, (const R*)B.cicw, M,
+                                                                 0, (R*)B.rho, inv_nbar);
+    return;
+  }
+  // M = 3 2^a: sort the particles by row-major mesh cell (scratch: key2 and
+  // prefix for the keys, idx2 and mend for the indices), CSR table of cells
+  uint64_t* ka = B.key2;
+  uint64_t* kb = (uint64_t*)B.prefix;
+  uint32_t* va = B.idx2;
+  uint32_t* vb = (uint32_t*)B.mend;
+  k_mesh_keys<<<grid_for(c->N0), kThreads, 0, c->stream>>>(B.n, c->cap, B.u, M, ka);
+  launch_sort_keys(c, ka, kb, va, vb, 4);  // M^3 < 2^32
+  k_cell_start<<<grid_for(c->N0 + 1), kThreads, 0, c->stream>>>(B.n, ka, 0, m3, B.cell_start);
+  k_cic_cellw_perm<R><<<grid_for(c->N0), kThreads, 0, c->stream>>>(B.n, c->cap, ka, va, B.u, B.k, M, (R*)B.cicw);
+  k_cic_gather<R><<<(unsigned)(m3 / 512), 256, 0, c->stream>>>(B.cell_start, B.n, c->cap, (const R*)B.cicw, M, 1,
                                                                (R*)B.rho, inv_nbar);
 }
 
@@ -192,6 +280,11 @@ void pm_interp(dzs_ctx* c) {
   Buffers& B = c->B;
   const int M = c->M;
   R inv12dx = (R)(1.0 / (12.0 * c->P.box / M));
+  if (!c->mesh_pow2) {
+    k_pm_interp<R><<<grid_for(c->N0), kThreads, 0, c->stream>>>(B.n, c->cap, B.u, (const R*)B.phi, M, inv12dx,
+                                                                (R*)B.g);
+    return;
+  }
   const int64_t tiles = (int64_t)(M / 8) * (M / 8) * (M / 8);
   const size_t sm = (2197 + 3 * 729) * sizeof(R);
   k_pm_interp_tile<R><<<(unsigned)tiles, 256, sm, c->stream>>>(B.cell_start, c->cap, B.u, (const R*)B.phi, M,
@@ -293,16 +386,15 @@ __global__ void k_sum_k2(const int32_t* __restrict__ d_n, const uint32_t* __rest
 }
 
 template <class R>
+void pm_deposit(dzs_ctx* c);
+
+template <class R>
 void pk_impl(dzs_ctx* c, int nbins, double* d_part, double* d_out, double shot) {
   Buffers& B = c->B;
   const int M = c->M;
   const int64_t m3 = (int64_t)M * M * M;
-  const int sh = 3 * (kMaxLevel - c->logM);
-  k_cell_start<<<grid_for(c->N0 + 1), kThreads, 0, c->stream>>>(B.n, B.key, sh, m3, B.cell_start);
-  R inv_nbar = (R)((double)m3 / (double)c->N0);
-  k_cic_cellw<R><<<grid_for(c->N0), kThreads, 0, c->stream>>>(B.n, c->cap, B.key, sh, B.u, B.k, M, (R*)B.cicw);
-  k_cic_gather<R><<<(unsigned)(m3 / 512), 256, 0, c->stream>>>(B.cell_start, B.n, c->cap, (const R*)B.cicw, M,
-                                                               (R*)B.rho, inv_nbar);
+  launch_cell_start(c);
+  pm_deposit<R>(c);
   fft_r2c_3d<R>(c, (const R*)B.rho, (cplx<R>*)B.spec, M, (const cplx<R>*)B.twiddle);
   const double L = c->P.box;
   const double norm = L * L * L / ((double)m3 * (double)m3);
@@ -318,7 +410,7 @@ void pk_impl(dzs_ctx* c, int nbins, double* d_part, double* d_out, double shot) 
 // [nbins][3]; d_part holds M * nbins * 3 doubles.  The state must be
 // Morton-sorted with valid keys.
 void launch_pk(dzs_ctx* c, int nbins, double* d_part, double* d_out, double shot) {
-  c->launches += 8;
+  c->launches += c->mesh_pow2 ? 8 : 21;
   if (c->fp64)
     pk_impl<double>(c, nbins, d_part, d_out, shot);
   else
@@ -337,13 +429,13 @@ void launch_sum_k2(dzs_ctx* c, unsigned long long* out) {
 // CSR table of the depth-m Morton cells (m = log2 M) of the current keys
 void launch_cell_start(dzs_ctx* c) {
   c->launches += 1;
-  const int64_t m3 = (int64_t)c->M * c->M * c->M;
+  const int64_t ncell = (int64_t)1 << (3 * c->logM);  // M^3 for M = 2^m
   const int sh = 3 * (kMaxLevel - c->logM);
-  k_cell_start<<<grid_for(c->N0 + 1), kThreads, 0, c->stream>>>(c->B.n, c->B.key, sh, m3, c->B.cell_start);
+  k_cell_start<<<grid_for(c->N0 + 1), kThreads, 0, c->stream>>>(c->B.n, c->B.key, sh, ncell, c->B.cell_start);
 }
 
 void launch_pm_deposit(dzs_ctx* c) {
-  c->launches += 2;
+  c->launches += c->mesh_pow2 ? 2 : 16;
   if (c->fp64)
     pm_deposit<double>(c);
   else

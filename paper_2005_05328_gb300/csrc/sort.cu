@@ -150,6 +150,26 @@ __global__ void k_permute(const int32_t* __restrict__ d_n, int64_t cap, const ui
 
 }  // namespace
 
+// stable LSD radix sort of n keys (an even number of 8-bit passes from bit 0)
+// with their indices (identity on input); the result is in ka / va again
+void launch_sort_keys(dzs_ctx* c, uint64_t* ka, uint64_t* kb, uint32_t* va, uint32_t* vb, int passes) {
+  c->launches += 3 * passes;
+  Buffers& B = c->B;
+  int nb = (int)((c->cap + kTile - 1) / kTile);
+  uint32_t* rowtot = B.hist + (int64_t)kDigits * nb;
+  uint64_t *kin = ka, *kout = kb;
+  uint32_t *vin = va, *vout = vb;
+  for (int pass = 0; pass < passes; ++pass) {
+    int shift = 8 * pass;
+    k_hist<<<nb, kSortThreads, 0, c->stream>>>(kin, B.n, shift, B.hist, nb);
+    k_scan_rows<<<kDigits, 1024, 0, c->stream>>>(B.hist, nb, rowtot);
+    k_scatter<<<nb, kSortThreads, 0, c->stream>>>(kin, vin, kout, vout, B.n, shift, B.hist, nb, rowtot,
+                                                  pass == 0);
+    std::swap(kin, kout);
+    std::swap(vin, vout);
+  }
+}
+
 void launch_sort(dzs_ctx* c) {
   c->launches += 25;
   Buffers& B = c->B;
