@@ -107,6 +107,43 @@ def serving_sample(dzs, nreq, warm):
                     "grows and p99 grows with the number of requests (no steady state)"}
 
 
+def batched_sample(dzs):
+    """The batched configuration: 64 mocks (16 each of N1 = 32, 48, 64, 96; L =
+    2 N1 Mpc/h, mesh 2 N1; seeds 1000 + i; sigma8 = 0.7 + 0.2 U, U from
+    SplitMix64(4242)), all admitted at once by the serving loop, FP32."""
+    st, reqs = 4242, []
+    for i in range(64):
+        st, z = splitmix64(st)
+        n1 = (32, 48, 64, 96)[i % 4]
+        reqs.append(dict(arrival_s=0.0, n1d=n1, mesh=2 * n1, box=2.0 * n1, sigma8=0.7 + 0.2 * (z >> 11) / 2.0 ** 53,
+                         seed=1000 + i))
+    status, wall, res = dzs.dzs_serve(reqs, hbm_budget_bytes=SERVE_BUDGET, steps_per_slice=8, precision=dzs.FP32)
+    work = sum(q["n1d"] ** 3 * 96 for q in reqs)
+    return {"mocks": 64, "status": status, "wall_s": wall, "particle_steps_per_s": work / wall,
+            "mocks_per_h": 64 * 3600.0 / wall, "sum_N": sum(q["n1d"] ** 3 for q in reqs)}
+
+
+def c3_sample(dzs, stream, steps=4):
+    """512^3 particles in 1024 Mpc/h, mesh 512^3, 128 steps, merge level 4: the
+    ICs, then `steps` steps at z ~ 49 timed (CUDA events on the stream)"""
+    import torch
+    P = dzs.params(n1d=512, mesh=512, box=1024.0, merge_level=4, nsteps=128, seed=3, precision=dzs.FP32)
+    ctx = dzs.Context(P, stream=stream.cuda_stream)
+    with torch.cuda.stream(stream):
+        ctx.ics()
+        ctx.step(1)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.step(steps)
+        b.record(stream)
+        b.synchronize()
+    ms = a.elapsed_time(b)
+    ctx.close()
+    return {"workload": "512^3, L = 1024 Mpc/h, mesh 512^3, FP32, steps 1..%d (z ~ 49)" % steps,
+            "ms_per_step": ms / steps, "particle_steps_per_s": 512 ** 3 * steps / (ms / 1e3)}
+
+
 def cufft_compare(stream, M, iters=20):
     """cuFFT (through torch.fft) r2c + Green-like multiply + c2r of an M^3 FP32
     mesh, the library comparison for the hand-written FFT stage"""
@@ -467,8 +504,12 @@ def main():
                                                 "note": "torch.fft (cuFFT) rfftn * G + irfftn, FP32, same mesh"}
         line["comparisons"] = comp
     line["config"]["mocks_per_h_single_stream"] = 3600.0 / (P.nsteps * ms / args.steps / 1e3)
+    line["config"]["actual_particle_steps_per_s"] = sum(counts) / (ms / 1e3)  # sum of N_active per step
     if world == 1 and args.serve_requests > 0:
         line["serving"] = serving_sample(dzs, args.serve_requests, 4)
+    if world == 1 and not args.no_compare:
+        line["batched"] = batched_sample(dzs)
+        line["large_instance"] = c3_sample(dzs, stream)
     if world == 1 and not args.no_cpu_baseline:
         try:
             line["cpu_baseline"] = cpu_baseline()
