@@ -118,7 +118,7 @@ struct Plan {
     o_idx2 = L.take(4 * cap);
     o_hist = L.take(4 * (257 * nb + 256));
     o_blocksum = L.take(8 * 4 * (nchunks + 2));
-    o_iscan = L.take(4 * (2 * cap + 4));
+    o_iscan = L.take(4 * (2 * cap + 64));  // also the tree's per-tile counts (23 per 1024 particles)
     o_prefix = L.take(8 * 4 * (cap + 1));
     o_mend = L.take(4 * cap);
     o_nodes = L.take(sizeof(Node) * node_cap);

@@ -1,21 +1,34 @@
 // tree.cu -- oct-tree over the Morton-sorted particles (paper Sec. 2.1: root =
 // box, nodes split into octants, nodes carry mass and centre of mass).
 //
-// Top-down, one launch per depth: a node with more than B particles (and depth
-// < 21) finds its non-empty octants and appends them to the next depth with
-// one atomic allocation.  Down to the PM mesh depth m (M = 2^m) the octant
-// boundaries are read from the CSR table of the depth-m Morton cells (the PM
-// deposit uses the same table), so the few huge nodes near the root cost O(1)
-// instead of long chains of dependent binary-search loads; deeper nodes are
-// small and search their keys.  Node numbering within a depth depends on
-// scheduling, the tree structure does not: every consumer walks structure
-// (children in octant order), so results are deterministic.  Bottom-up, in
-// one launch: every leaf sums its particles, then climbs -- the last child to
-// arrive at a parent (atomic counter) sums the children and goes on, the
-// others stop; nothing waits.  Exact integer mass and mass-weighted position
-// (uint64), the rounded integer COM and the largest member multiplicity (node
-// softening).  Walk groups (node with <= G particles whose parent holds more,
-// or a leaf) are listed in Morton order.
+// The tree is the top-down one (a cell is split when it holds more than B
+// particles and is above depth 21), built without a pass per depth.  Every
+// node is a Morton cell and starts at a particle: the particle i that opens a
+// cell at depth j (its key differs from key[i-1] within the first j octal
+// digits, i.e. L_i < j with L_i the digits key[i-1] and key[i] share) owns
+// that node exactly when the enclosing depth-(j-1) cell holds more than B
+// particles -- when some run of B + 1 consecutive sorted keys around i shares
+// j - 1 digits.  So particle i owns the depths L_i < j <= J_i, with
+// J_i = min(21, 1 + max over a in [i-B, i] of lcp(key[a], key[a+B])), and its
+// node at depth j is internal iff j < J_i.  Likewise (with G for B) the walk
+// group of i's chain sits at depth min(J_i, 1 + max lcp over the G-runs).
+//
+// Nodes are numbered depth by depth, each depth in Morton order, so the
+// children of a node are consecutive: a count pass per tile of particles, a
+// scan of the per-tile counts of each depth, then a pass in which each owner
+// writes its nodes.  A node's first child index is the number of depth-(j+1)
+// nodes before its start; the child count is the difference to the next node
+// of the same depth.  Node boundaries: down to the PM mesh depth m the cell
+// ends come from the CSR table of the depth-m Morton cells; deeper, a binary
+// search of the keys inside the parent's range.  The numbering depends only
+// on the keys (no atomics), so the tree is deterministic.
+//
+// Bottom-up, in one launch: every leaf sums its particles, then climbs -- the
+// last child to arrive at a parent (atomic counter) sums the children and goes
+// on, the others stop; nothing waits.  Exact integer mass and mass-weighted
+// position (uint64), the rounded integer COM and the largest member
+// multiplicity (node softening).  Walk groups (node with <= G particles whose
+// parent holds more, or a leaf) are listed in Morton order.
 #include <cuda/atomic>
 
 #include "common.cuh"
@@ -23,26 +36,15 @@
 namespace dzs {
 namespace {
 
-__global__ void k_tree_root(const int32_t* __restrict__ d_n, Node* __restrict__ nodes, int32_t* __restrict__ lvl,
-                            int32_t* __restrict__ group_head, int32_t* __restrict__ parent, int G) {
-  int t = threadIdx.x;
-  if (t < kMaxLevel + 2) lvl[t] = 0;
-  if (t == 0) {
-    parent[0] = -1;
-    int32_t n = *d_n;
-    Node r;
-    r.cx = r.cy = r.cz = 0x80000000u;
-    r.comx = r.comy = r.comz = 0x80000000u;
-    r.mass = 0;
-    r.kmax = 0;
-    r.start = 0;
-    r.count = n;
-    r.child = -1;
-    r.meta = 0;
-    nodes[0] = r;
-    lvl[0] = n > 0 ? 1 : 0;
-    if (n > 0 && n <= G) group_head[0] = 0;
-  }
+constexpr int kTreeTile = 1024;          // particles per block (one per thread)
+constexpr int kHalo = 64;                // largest G (walk_group <= 64)
+constexpr int kCols = kMaxLevel + 2;     // node counts per depth 0..21, then walk groups
+constexpr unsigned kFull = 0xffffffffu;
+
+// octal digits shared by two keys (21 for equal keys); keys are < 2^63
+__device__ __forceinline__ int lcp_digits(uint64_t a, uint64_t b) {
+  const uint64_t x = a ^ b;
+  return x == 0 ? kMaxLevel : (__clzll((long long)x) - 1) / 3;
 }
 
 __device__ __forceinline__ int64_t lb(const uint64_t* __restrict__ key, int64_t lo, int64_t hi, uint64_t x) {
@@ -56,66 +58,238 @@ __device__ __forceinline__ int64_t lb(const uint64_t* __restrict__ key, int64_t 
   return lo;
 }
 
-__global__ void k_tree_down(int level, const uint64_t* __restrict__ key, const int32_t* __restrict__ cstart,
-                            int depth_m, Node* __restrict__ nodes, int32_t* __restrict__ lvl,
-                            int32_t* __restrict__ group_head, int32_t* __restrict__ parent,
-                            int32_t* __restrict__ arrive, int64_t node_cap, int B, int G,
-                            uint32_t* __restrict__ err) {
-  int64_t base = 0;
-  for (int j = 0; j < level; ++j) base += lvl[j];
-  const int64_t cnt = lvl[level];
-  const int64_t child_base = base + cnt;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t ni = base + t;
-    Node nd = nodes[ni];
-    if (nd.count <= B || level == kMaxLevel) continue;  // leaf
-    const int64_t s = nd.start, e = (int64_t)nd.start + nd.count;
-    const int sh = 3 * (kMaxLevel - (level + 1));
-    const uint64_t pref = (key[s] >> (sh + 3)) << 3;  // parent prefix, shifted to child digit
-    int64_t bnd[9];
-    bnd[0] = s;
-    bnd[8] = e;
-    if (level + 1 <= depth_m) {
-      // child cell (pref | d) at depth level + 1 starts where its first
-      // depth-m sub-cell starts
-      const int dsh = 3 * (depth_m - (level + 1));
-      for (int d = 1; d < 8; ++d) bnd[d] = cstart[(pref | (uint64_t)d) << dsh];
+// per particle: L_i, J_i and the group depth g_i (packed into info[i]); per
+// tile: the number of nodes of each depth and of walk groups its particles own
+__global__ void __launch_bounds__(kTreeTile) k_tree_count(const int32_t* __restrict__ d_n,
+                                                          const uint64_t* __restrict__ key, int B, int G,
+                                                          int32_t* __restrict__ info, int32_t* __restrict__ tcount,
+                                                          int64_t ntiles) {
+  __shared__ uint64_t ks[kTreeTile + 2 * kHalo];  // keys t0 - kHalo .. t0 + kTreeTile + kHalo
+  __shared__ int8_t wb[kTreeTile + kHalo], wg[kTreeTile + kHalo];  // runs starting at t0 - kHalo + q
+  __shared__ int32_t wcnt[kTreeTile / 32][kCols];
+  const int64_t n = *d_n;
+  const int64_t t0 = (int64_t)blockIdx.x * kTreeTile;
+  for (int q = threadIdx.x; q < kTreeTile + 2 * kHalo; q += kTreeTile) {
+    const int64_t a = t0 - kHalo + q;
+    ks[q] = (a >= 0 && a < n) ? key[a] : 0ull;
+  }
+  for (int q = threadIdx.x; q < (kTreeTile / 32) * kCols; q += kTreeTile) (&wcnt[0][0])[q] = 0;
+  __syncthreads();
+  for (int q = threadIdx.x; q < kTreeTile + kHalo; q += kTreeTile) {
+    const int64_t a = t0 - kHalo + q;
+    wb[q] = (int8_t)((a >= 0 && a + B < n) ? lcp_digits(ks[q], ks[q + B]) : -1);
+    wg[q] = (int8_t)((a >= 0 && a + G < n) ? lcp_digits(ks[q], ks[q + G]) : -1);
+  }
+  __syncthreads();
+  const int64_t i = t0 + threadIdx.x;
+  const int q = threadIdx.x + kHalo;
+  const bool valid = i < n;
+  int L = 0, J = -1, g = -1;
+  if (valid) {
+    L = i > 0 ? lcp_digits(ks[q - 1], ks[q]) : -1;
+    int mb = -1, mg = -1;
+    for (int d = 0; d <= B; ++d) mb = max(mb, (int)wb[q - d]);
+    for (int d = 0; d <= G; ++d) mg = max(mg, (int)wg[q - d]);
+    J = min(kMaxLevel, 1 + mb);
+    g = min(J, 1 + mg);
+    info[i] = (L + 1) | (J << 8) | (g << 16);
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const bool owner = valid && L < J;
+  const int jlo = __reduce_min_sync(kFull, owner ? L + 1 : kMaxLevel + 1);
+  const int jhi = __reduce_max_sync(kFull, owner ? J : -1);
+  for (int j = jlo; j <= jhi; ++j) {
+    const unsigned b = __ballot_sync(kFull, owner && L < j && j <= J);
+    if (lane == 0) wcnt[w][j] = __popc(b);
+  }
+  const unsigned bg = __ballot_sync(kFull, valid && L < g);
+  if (lane == 0) wcnt[w][kCols - 1] = __popc(bg);
+  __syncthreads();
+  if (threadIdx.x < kCols) {
+    int s = 0;
+    for (int ww = 0; ww < kTreeTile / 32; ++ww) s += wcnt[ww][threadIdx.x];
+    tcount[(int64_t)threadIdx.x * ntiles + blockIdx.x] = s;
+  }
+}
+
+// block c: exclusive scan of column c of the tile counts, column total to tot[c]
+__global__ void k_tree_scan(int32_t* __restrict__ tcount, int64_t ntiles, int32_t* __restrict__ tot) {
+  __shared__ int32_t warp_tot[32];
+  __shared__ int32_t carry;
+  int32_t* col = tcount + (int64_t)blockIdx.x * ntiles;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int64_t b0 = 0; b0 < ntiles; b0 += blockDim.x) {
+    const int64_t b = b0 + threadIdx.x;
+    const int32_t v = b < ntiles ? col[b] : 0;
+    int32_t inc = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t t = __shfl_up_sync(kFull, inc, o);
+      if (lane >= o) inc += t;
+    }
+    if (lane == 31) warp_tot[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+      const int32_t t = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0;
+      int32_t ti = t;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int32_t u = __shfl_up_sync(kFull, ti, o);
+        if (lane >= o) ti += u;
+      }
+      warp_tot[lane] = ti - t;
+    }
+    __syncthreads();
+    const int32_t ex = inc - v + warp_tot[w] + carry;
+    if (b < ntiles) col[b] = ex;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry = ex + v;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) tot[blockIdx.x] = carry;
+}
+
+// node counts per depth and the group count; a tree above the node capacity
+// is not built (error bit, zero nodes and groups)
+__global__ void k_tree_totals(int32_t* __restrict__ lvl, int64_t node_cap, uint64_t* __restrict__ counters,
+                              uint32_t* __restrict__ err) {
+  if (threadIdx.x != 0) return;
+  int64_t total = 0;
+  for (int j = 0; j <= kMaxLevel; ++j) total += lvl[j];
+  if (total > node_cap) {
+    atomicOr(err, kErrNodes);
+    for (int j = 0; j < kCols; ++j) lvl[j] = 0;
+    total = 0;
+  }
+  counters[2] = (uint64_t)lvl[kCols - 1];
+  counters[3] = (uint64_t)total;
+}
+
+// every owner writes its nodes: index = (nodes of shallower depths) + (nodes of
+// the same depth starting before it); first-child index to cfirst
+__global__ void __launch_bounds__(kTreeTile) k_tree_nodes(
+    const int32_t* __restrict__ d_n, int64_t cap, const uint64_t* __restrict__ key, const uint32_t* __restrict__ u,
+    const int32_t* __restrict__ info, const int32_t* __restrict__ tcount, int64_t ntiles,
+    const int32_t* __restrict__ lvl, const int32_t* __restrict__ cstart, int depth_m, int B, Node* __restrict__ nodes,
+    int32_t* __restrict__ cfirst, int32_t* __restrict__ parent, int32_t* __restrict__ arrive,
+    int32_t* __restrict__ groups) {
+  __shared__ int32_t wcnt[kTreeTile / 32][kCols];
+  __shared__ int32_t base[kCols];
+  const int64_t n = *d_n;
+  const int64_t t0 = (int64_t)blockIdx.x * kTreeTile;
+  if (threadIdx.x == 0) {
+    int32_t s = 0;
+    for (int j = 0; j <= kMaxLevel; ++j) {
+      base[j] = s + tcount[(int64_t)j * ntiles + blockIdx.x];
+      s += lvl[j];
+    }
+    base[kCols - 1] = tcount[(int64_t)(kCols - 1) * ntiles + blockIdx.x];
+    base[0] = s == 0 ? -1 : base[0];  // no tree (empty or over capacity)
+  }
+  for (int q = threadIdx.x; q < (kTreeTile / 32) * kCols; q += kTreeTile) (&wcnt[0][0])[q] = 0;
+  __syncthreads();
+  if (base[0] < 0) return;
+  const int64_t i = t0 + threadIdx.x;
+  const bool valid = i < n;
+  int L = 0, J = -1, g = -1;
+  if (valid) {
+    const int32_t v = info[i];
+    L = (v & 0xff) - 1;
+    J = (v >> 8) & 0xff;
+    g = (v >> 16) & 0xff;
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  const bool owner = valid && L < J;
+  // depths whose ranks this warp needs: its nodes' depths and one below
+  const int jlo = __reduce_min_sync(kFull, owner ? L + 1 : kMaxLevel + 1);
+  const int jhi = min(kMaxLevel, __reduce_max_sync(kFull, owner ? J + 1 : -1));
+  for (int j = jlo; j <= jhi; ++j) {
+    const unsigned b = __ballot_sync(kFull, owner && L < j && j <= J);
+    if (lane == 0) wcnt[w][j] = __popc(b);
+  }
+  const unsigned bg = __ballot_sync(kFull, valid && L < g);
+  if (lane == 0) wcnt[w][kCols - 1] = __popc(bg);
+  __syncthreads();
+  // lane c holds the first index of column c for this warp
+  int32_t wbase = 0;
+  if (lane < kCols) {
+    wbase = base[lane];
+    for (int ww = 0; ww < w; ++ww) wbase += wcnt[ww][lane];
+  }
+  const uint64_t k = valid ? key[i] : 0ull;
+  const uint32_t ux = valid ? u[i] : 0u, uy = valid ? u[cap + i] : 0u, uz = valid ? u[2 * cap + i] : 0u;
+  int32_t prev = -1;      // index of this particle's node one depth up
+  int64_t prev_end = 0;   // its end
+  int32_t gnode = -1;
+  for (int j = jlo; j <= jhi; ++j) {
+    const bool mine = owner && L < j && j <= J;
+    const unsigned b = __ballot_sync(kFull, mine);
+    const int32_t rank = __shfl_sync(kFull, wbase, j) + __popc(b & lt);
+    if (prev >= 0) cfirst[prev] = rank;  // depth-j nodes before this particle
+    if (!mine) {
+      prev = -1;
+      continue;
+    }
+    const int sh = 3 * (kMaxLevel - j);
+    const uint64_t pref = k >> sh;
+    int64_t end;
+    if (j <= depth_m) {
+      end = cstart[(pref + 1) << (3 * (depth_m - j))];
     } else {
-      for (int d = 1; d < 8; ++d) bnd[d] = lb(key, bnd[d - 1], e, (pref | (uint64_t)d) << sh);
+      int64_t hi = prev >= 0 ? prev_end : (int64_t)cstart[(k >> (3 * (kMaxLevel - depth_m))) + 1];
+      if (j == J && J < kMaxLevel) hi = min(hi, i + B + 1);  // a leaf above depth 21 holds <= B
+      end = lb(key, i + 1, hi, (pref + 1) << sh);
     }
-    int nch = 0;
-    for (int d = 0; d < 8; ++d) nch += (bnd[d + 1] > bnd[d]) ? 1 : 0;
-    int64_t off = atomicAdd(&lvl[level + 1], nch);
-    int64_t first = child_base + off;
-    if (first + nch > node_cap) {
-      atomicOr(err, kErrNodes);
-      continue;  // left as a leaf: the walk then sums its particles directly
+    const uint32_t half = 1u << (31 - j);
+    const uint32_t mask = j == 0 ? 0u : ~((half << 1) - 1u);
+    Node c;
+    c.cx = (ux & mask) | half;
+    c.cy = (uy & mask) | half;
+    c.cz = (uz & mask) | half;
+    c.comx = c.comy = c.comz = 0;
+    c.mass = 0;
+    c.kmax = 0;
+    c.start = (int32_t)i;
+    c.count = (int32_t)(end - i);
+    c.child = j < J ? 0 : -1;  // internal: linked by k_tree_link
+    c.meta = (uint32_t)j;
+    nodes[rank] = c;
+    if (j < J) arrive[rank] = 0;
+    if (j == 0) parent[rank] = -1;
+    if (j == g) gnode = rank;
+    prev = rank;
+    prev_end = end;
+  }
+  if (prev >= 0) cfirst[prev] = 0;  // depth 21: no children
+  const int32_t gbase = __shfl_sync(kFull, wbase, kCols - 1);  // all lanes take part
+  if (valid && L < g) groups[gbase + __popc(bg & lt)] = gnode;
+}
+
+// internal nodes: first child and child count (to the next node of the same
+// depth, or to the end of the next depth), parent links of the children
+__global__ void k_tree_link(const int32_t* __restrict__ lvl, Node* __restrict__ nodes,
+                            const int32_t* __restrict__ cfirst, int32_t* __restrict__ parent) {
+  __shared__ int32_t lb_[kMaxLevel + 3];
+  if (threadIdx.x == 0) {
+    int32_t s = 0;
+    for (int j = 0; j <= kMaxLevel; ++j) {
+      lb_[j] = s;
+      s += lvl[j];
     }
-    const uint32_t lc = 1u << (31 - level);  // child side 2^(32 - level - 1)
-    int q = 0;
-    for (int d = 0; d < 8; ++d) {
-      if (bnd[d + 1] == bnd[d]) continue;
-      Node c;
-      const uint32_t h = lc >> 1;
-      c.cx = (d & 4) ? nd.cx + h : nd.cx - h;
-      c.cy = (d & 2) ? nd.cy + h : nd.cy - h;
-      c.cz = (d & 1) ? nd.cz + h : nd.cz - h;
-      c.comx = c.comy = c.comz = 0;
-      c.mass = 0;
-      c.kmax = 0;
-      c.start = (int32_t)bnd[d];
-      c.count = (int32_t)(bnd[d + 1] - bnd[d]);
-      c.child = -1;
-      c.meta = (uint32_t)(level + 1);
-      nodes[first + q] = c;
-      parent[first + q] = (int32_t)ni;
-      bool leaf = c.count <= B || level + 1 == kMaxLevel;
-      if (nd.count > G && (c.count <= G || leaf)) group_head[c.start] = (int32_t)(first + q);
-      ++q;
-    }
-    nodes[ni].child = (int32_t)first;
-    nodes[ni].meta = (uint32_t)level | ((uint32_t)nch << 8);
-    arrive[ni] = 0;
+    lb_[kMaxLevel + 1] = s;
+    lb_[kMaxLevel + 2] = s;
+  }
+  __syncthreads();
+  const int64_t total = lb_[kMaxLevel + 1];
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    if (nodes[t].child < 0) continue;
+    const int j = (int)(nodes[t].meta & 0xff);
+    const int32_t c0 = cfirst[t];
+    const int32_t c1 = (t + 1 < lb_[j + 1]) ? cfirst[t + 1] : lb_[j + 2];
+    nodes[t].child = c0;
+    nodes[t].meta = (uint32_t)j | ((uint32_t)(c1 - c0) << 8);
+    for (int32_t q = c0; q < c1; ++q) parent[q] = (int32_t)t;
   }
 }
 
@@ -176,49 +350,28 @@ __global__ void k_tree_up_all(const int32_t* __restrict__ lvl, int64_t cap, cons
   }
 }
 
-__global__ void k_group_flags(const int32_t* __restrict__ d_n, const int32_t* __restrict__ head,
-                              int32_t* __restrict__ flag) {
-  const int64_t n = *d_n;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    flag[i] = head[i] >= 0 ? 1 : 0;
-}
-
-__global__ void k_group_list(const int32_t* __restrict__ d_n, const int32_t* __restrict__ head,
-                             const int32_t* __restrict__ rank, int32_t* __restrict__ groups,
-                             uint64_t* __restrict__ counters, const int32_t* __restrict__ lvl) {
-  const int64_t n = *d_n;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    if (head[i] >= 0) groups[rank[i]] = head[i];
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    counters[2] = (uint64_t)rank[n];
-    uint64_t tot = 0;
-    for (int j = 0; j <= kMaxLevel; ++j) tot += (uint64_t)lvl[j];
-    counters[3] = tot;
-  }
-}
-
 }  // namespace
 
 void launch_tree(dzs_ctx* c) {
-  c->launches += 28;
+  c->launches += 6;
   Buffers& B = c->B;
   // the depth-m Morton cell table (also the PM deposit's)
   launch_cell_start(c);
-  cudaMemsetAsync(B.group_head, 0xff, sizeof(int32_t) * c->cap, c->stream);
-  k_tree_root<<<1, 32, 0, c->stream>>>(B.n, B.nodes, B.lvl_count, B.group_head, B.parent, c->P.walk_group);
-  int grid = grid_for(c->N0, kThreads, 152 * 2);
-  for (int j = 0; j < kMaxLevel; ++j)
-    k_tree_down<<<grid, kThreads, 0, c->stream>>>(j, B.key, B.cell_start, c->logM, B.nodes, B.lvl_count,
-                                                  B.group_head, B.parent, B.arrive, c->node_cap, c->P.leaf_bucket,
-                                                  c->P.walk_group, B.err);
+  const int64_t ntiles = (c->cap + kTreeTile - 1) / kTreeTile;
+  int32_t* info = B.group_head;       // [cap] per-particle L, J, g
+  int32_t* tcount = B.iscan;          // [kCols][ntiles] tile counts, then offsets
+  int32_t* cfirst = (int32_t*)B.nsum; // [node_cap] (the sums are written after)
+  k_tree_count<<<(unsigned)ntiles, kTreeTile, 0, c->stream>>>(B.n, B.key, c->P.leaf_bucket, c->P.walk_group, info,
+                                                              tcount, ntiles);
+  k_tree_scan<<<kCols, 1024, 0, c->stream>>>(tcount, ntiles, B.lvl_count);
+  k_tree_totals<<<1, 32, 0, c->stream>>>(B.lvl_count, c->node_cap, B.counters, B.err);
+  k_tree_nodes<<<(unsigned)ntiles, kTreeTile, 0, c->stream>>>(B.n, c->cap, B.key, B.u, info, tcount, ntiles,
+                                                              B.lvl_count, B.cell_start, c->logM, c->P.leaf_bucket,
+                                                              B.nodes, cfirst, B.parent, B.arrive, B.groups);
+  k_tree_link<<<grid_for(c->node_cap, kThreads, 152 * 8), kThreads, 0, c->stream>>>(B.lvl_count, B.nodes, cfirst,
+                                                                                     B.parent);
   k_tree_up_all<<<grid_for(c->node_cap, kThreads, 152 * 8), kThreads, 0, c->stream>>>(
       B.lvl_count, c->cap, B.u, B.k, B.nodes, B.nsum, c->node_cap, B.parent, B.arrive);
-  int32_t* flag = B.iscan + (c->cap + 1);
-  int32_t* rank = B.iscan;
-  k_group_flags<<<grid_for(c->N0), kThreads, 0, c->stream>>>(B.n, B.group_head, flag);
-  exclusive_scan_i32(c, flag, rank, B.n, c->cap);
-  k_group_list<<<grid_for(c->N0), kThreads, 0, c->stream>>>(B.n, B.group_head, rank, B.groups, B.counters,
-                                                            B.lvl_count);
 }
 
 }  // namespace dzs
