@@ -40,9 +40,38 @@ __device__ __forceinline__ R frac32(uint32_t lo) {
   return (R)lo * (R)2.3283064365386963e-10;  // 2^-32
 }
 
-// W[o][first particle of a cell] = sum over the cell's particles, in order, of
-// k w_o, w_o the CIC weight of the cell's corner node o = (ox, oy, oz): each
-// particle's weights are computed once (not once per node that reads it)
+// 16-byte vectors of R (aligned loads and stores of 8 weights or a phi row)
+template <class R>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using T = float4;
+  static constexpr int N = 4;
+};
+template <>
+struct Vec16<double> {
+  using T = double2;
+  static constexpr int N = 2;
+};
+
+template <class R>
+__device__ __forceinline__ void store8(R* __restrict__ dst, const R (&v)[8]) {
+  using V = typename Vec16<R>::T;
+  constexpr int N = Vec16<R>::N;
+#pragma unroll
+  for (int q = 0; q < 8 / N; ++q) {
+    V x;
+    R* xs = reinterpret_cast<R*>(&x);
+#pragma unroll
+    for (int r = 0; r < N; ++r) xs[r] = v[q * N + r];
+    reinterpret_cast<V*>(dst)[q] = x;
+  }
+}
+
+// W[8 i + o], i the first particle of a cell = sum over the cell's particles,
+// in order, of k w_o, w_o the CIC weight of the cell's corner node
+// o = (ox, oy, oz): each particle's weights are computed once (not once per
+// node that reads it); the 8 sums of a cell are one aligned 8-value record
 template <class R>
 __global__ void k_cic_cellw(const int32_t* __restrict__ d_n, int64_t cap, const uint64_t* __restrict__ key, int sh,
                             const uint32_t* __restrict__ u, const uint32_t* __restrict__ k, int M,
@@ -63,8 +92,7 @@ __global__ void k_cic_cellw(const int32_t* __restrict__ d_n, int64_t cap, const 
         acc[o] += kk * ((ox ? fx : (R)1 - fx) * (oy ? fy : (R)1 - fy) * (oz ? fz : (R)1 - fz));
       }
     }
-#pragma unroll
-    for (int o = 0; o < 8; ++o) W[o * cap + i] = acc[o];
+    store8(W + 8 * i, acc);
   }
 }
 
@@ -92,8 +120,7 @@ __global__ void k_cic_cellw_perm(const int32_t* __restrict__ d_n, int64_t cap, c
         acc[o] += kk * ((ox ? fx : (R)1 - fx) * (oy ? fy : (R)1 - fy) * (oz ? fz : (R)1 - fz));
       }
     }
-#pragma unroll
-    for (int o = 0; o < 8; ++o) W[o * cap + t] = acc[o];
+    store8(W + 8 * t, acc);
   }
 }
 
@@ -108,41 +135,101 @@ __global__ void k_mesh_keys(const int32_t* __restrict__ d_n, int64_t cap, const 
 }
 
 // rho[node] = sum over the 8 cells node - o, o in {0,1}^3, of the cell's
-// corner-o weight sum; output delta.  One block per 8^3 tile of nodes: the CSR
-// bounds of the 9^3 cells the tile touches are staged in shared memory once;
-// each node sums its 8 cells in a fixed order, so the mesh is deterministic.
-template <class R>
+// corner-o weight sum; output delta.  One block per 8^3 tile of nodes:
+//   1. the CSR bounds of the 9^3 cells the tile touches: for Morton-ordered
+//      cells the tile's own 8^3 cells are one run of the table (513
+//      consecutive entries, coalesced) and only the 217 cells of the three
+//      lower halo planes are looked up one by one;
+//   2. the 8 weight sums of every non-empty cell (one 8-value record each)
+//      into shared memory, zeros for empty cells;
+//   3. each node adds its 8 cells in the fixed order o = 0..7 (empty cells
+//      add +0), so the mesh is deterministic.
+template <class R, bool kMorton>
 __global__ void __launch_bounds__(256) k_cic_gather(const int32_t* __restrict__ start, const int32_t* __restrict__ d_n,
-                                                    int64_t cap, const R* __restrict__ W, int M, int rowmajor,
-                                                    R* __restrict__ delta, R inv_nbar) {
-  __shared__ int32_t cs[729], ce[729];
+                                                    const R* __restrict__ W, int M, R* __restrict__ delta,
+                                                    R inv_nbar) {
+  extern __shared__ unsigned char cg_raw[];
+  R* wv = reinterpret_cast<R*>(cg_raw);                   // [8][729]
+  int32_t* first = reinterpret_cast<int32_t*>(wv + 8 * 729);  // [729] first particle, -1 empty
+  int32_t* sb = first + 729;                               // [513] the tile's own bounds
   const int T = M >> 3;
   const int tile = blockIdx.x;
-  const int bx = (tile / (T * T)) * 8, by = ((tile / T) % T) * 8, bz = (tile % T) * 8;
+  const int tx = tile / (T * T), ty = (tile / T) % T, tz = tile % T;
+  const int bx = tx * 8, by = ty * 8, bz = tz * 8;
   const int32_t n = *d_n;
-  const int mask = M - 1;
-  for (int q = threadIdx.x; q < 729; q += blockDim.x) {
-    int i = q / 81, j = (q / 9) % 9, l = q % 9;
+  auto clampb = [n](int32_t v) { return v < 0 ? 0 : (v > n ? n : v); };
+  auto cell_of = [&](int i, int j, int l) -> int64_t {  // 9^3 coordinates (offset -1)
     const uint32_t gx = (uint32_t)((bx + i - 1 + M) % M), gy = (uint32_t)((by + j - 1 + M) % M),
                    gz = (uint32_t)((bz + l - 1 + M) % M);
-    const int64_t mc = rowmajor ? ((int64_t)gx * M + gy) * M + gz : (int64_t)morton_cell(gx, gy, gz);
-    int32_t s = start[mc], e = start[mc + 1];
-    s = s < 0 ? 0 : s;  // defensive: the table is consistent for sorted keys
-    e = e > n ? n : e;
-    cs[q] = s;
-    ce[q] = e < s ? s : e;
+    return kMorton ? (int64_t)morton_cell(gx, gy, gz) : ((int64_t)gx * M + gy) * M + gz;
+  };
+  if (kMorton) {
+    const int64_t base =
+        (int64_t)((spread3((uint32_t)tx) << 2) | (spread3((uint32_t)ty) << 1) | spread3((uint32_t)tz)) << 9;
+    for (int mo = threadIdx.x; mo <= 512; mo += blockDim.x) sb[mo] = clampb(start[base + mo]);
+    for (int h = threadIdx.x; h < 217; h += blockDim.x) {
+      int i, j, l;
+      if (h < 81) {
+        i = 0, j = h / 9, l = h % 9;
+      } else if (h < 153) {
+        i = 1 + (h - 81) / 9, j = 0, l = (h - 81) % 9;
+      } else {
+        i = 1 + (h - 153) / 8, j = 1 + (h - 153) % 8, l = 0;
+      }
+      const int64_t mc = cell_of(i, j, l);
+      const int32_t s0 = clampb(start[mc]), e0 = clampb(start[mc + 1]);
+      first[(i * 9 + j) * 9 + l] = e0 > s0 ? s0 : -1;
+    }
+    __syncthreads();
+    for (int mo = threadIdx.x; mo < 512; mo += blockDim.x) {
+      const int i = ((mo >> 6) & 4) | ((mo >> 4) & 2) | ((mo >> 2) & 1);
+      const int j = ((mo >> 5) & 4) | ((mo >> 3) & 2) | ((mo >> 1) & 1);
+      const int l = ((mo >> 4) & 4) | ((mo >> 2) & 2) | (mo & 1);
+      first[((i + 1) * 9 + (j + 1)) * 9 + (l + 1)] = sb[mo + 1] > sb[mo] ? sb[mo] : -1;
+    }
+  } else {
+    for (int q = threadIdx.x; q < 729; q += blockDim.x) {
+      const int64_t mc = cell_of(q / 81, (q / 9) % 9, q % 9);
+      const int32_t s0 = clampb(start[mc]), e0 = clampb(start[mc + 1]);
+      first[q] = e0 > s0 ? s0 : -1;
+    }
+  }
+  __syncthreads();
+  using V = typename Vec16<R>::T;
+  constexpr int N = Vec16<R>::N;
+  for (int q = threadIdx.x; q < 729; q += blockDim.x) {
+    const int32_t f = first[q];
+    if (f >= 0) {
+      const V* src = reinterpret_cast<const V*>(W + 8 * (int64_t)f);
+#pragma unroll
+      for (int v = 0; v < 8 / N; ++v) {
+        const V x = src[v];
+        const R* xs = reinterpret_cast<const R*>(&x);
+#pragma unroll
+        for (int r = 0; r < N; ++r) wv[(v * N + r) * 729 + q] = xs[r];
+      }
+    } else {
+#pragma unroll
+      for (int o = 0; o < 8; ++o) wv[o * 729 + q] = (R)0;
+    }
   }
   __syncthreads();
   for (int t = threadIdx.x; t < 512; t += blockDim.x) {
     const int a = t >> 6, b = (t >> 3) & 7, c = t & 7;
+    const int q0 = (a + 1) * 81 + (b + 1) * 9 + (c + 1);
     R acc = 0;
+#pragma unroll
     for (int o = 0; o < 8; ++o) {
-      int ox = (o >> 2) & 1, oy = (o >> 1) & 1, oz = o & 1;
-      int q = (a - ox + 1) * 81 + (b - oy + 1) * 9 + (c - oz + 1);
-      if (ce[q] > cs[q]) acc += W[o * cap + cs[q]];
+      const int ox = (o >> 2) & 1, oy = (o >> 1) & 1, oz = o & 1;
+      acc += wv[o * 729 + q0 - ox * 81 - oy * 9 - oz];
     }
     delta[((int64_t)(bx + a) * M + (by + b)) * M + (bz + c)] = acc * inv_nbar - (R)1;
   }
+}
+
+template <class R>
+constexpr size_t gather_smem() {
+  return 8 * 729 * sizeof(R) + (729 + 513) * sizeof(int32_t);
 }
 
 // g = -grad phi at the particles for any mesh (used for M = 3 2^a): the
@@ -179,17 +266,32 @@ __global__ void k_pm_interp(const int32_t* __restrict__ d_n, int64_t cap, const 
 
 // g = -grad phi (four-point stencil at the 8 surrounding nodes), CIC weights.
 // One block per 8^3 tile of cells = one depth-(m-3) octree cell, whose
-// particles are one contiguous Morton run: the block stages the 13^3 nodes of
-// phi the tile's stencils reach, forms the gradient at the 9^3 corner nodes in
-// shared memory (the same four-point formula per node), then interpolates
-// every particle of the tile from shared memory.
+// particles are one contiguous Morton run.  The block stages the 13^3 nodes of
+// phi the tile's stencils reach as 169 rows of 16 (z from bz - 4, aligned
+// 16-byte loads away from the periodic z edge), then either forms the
+// gradient at the 9^3 corner nodes once (many particles) or lets each
+// particle form its 8 corner gradients from the staged phi (few particles);
+// both use the same four-point formula, so the result does not depend on the
+// choice.
+constexpr int kFlyMax = 96;  // below this many particles a tile skips the node gradients
+
+template <class R>
+__device__ __forceinline__ void grad_at(const R* __restrict__ ph, int i, int j, int l, R& gx, R& gy, R& gz) {
+  // node (i, j, l) of the 9^3 corner block: phi row ((i + 2) * 13 + j + 2), z slot l + 4
+  auto P = [&](int x, int y, int z) -> R { return ph[(x * 13 + y) * 16 + z]; };
+  const int x = i + 2, y = j + 2, z = l + 4;
+  gx = (R)8 * (P(x + 1, y, z) - P(x - 1, y, z)) - (P(x + 2, y, z) - P(x - 2, y, z));
+  gy = (R)8 * (P(x, y + 1, z) - P(x, y - 1, z)) - (P(x, y + 2, z) - P(x, y - 2, z));
+  gz = (R)8 * (P(x, y, z + 1) - P(x, y, z - 1)) - (P(x, y, z + 2) - P(x, y, z - 2));
+}
+
 template <class R>
 __global__ void __launch_bounds__(256) k_pm_interp_tile(const int32_t* __restrict__ start, int64_t cap,
                                                         const uint32_t* __restrict__ u, const R* __restrict__ phi,
                                                         int M, R inv12dx, R* __restrict__ g) {
   extern __shared__ unsigned char pi_raw[];
-  R* ph = reinterpret_cast<R*>(pi_raw);  // [13][13][13], node (bx - 2 + i, ...)
-  R* gr = ph + 2197;                     // [3][9][9][9], corner node (bx + i, ...)
+  R* ph = reinterpret_cast<R*>(pi_raw);  // [169][16]: row (i, j) = node (bx - 2 + i, by - 2 + j), z = bz - 4 + slot
+  R* gr = ph + 169 * 16;                 // [3][9][9][9], corner node (bx + i, ...)
   const int T = M >> 3;
   const int tile = blockIdx.x;
   const int tx = tile / (T * T), ty = (tile / T) % T, tz = tile % T;
@@ -199,19 +301,34 @@ __global__ void __launch_bounds__(256) k_pm_interp_tile(const int32_t* __restric
   const int32_t p0 = start[(int64_t)tp << 9], p1 = start[((int64_t)tp + 1) << 9];
   if (p1 <= p0) return;  // empty tile (uniform across the block)
   const int mask = M - 1;
-  for (int q = threadIdx.x; q < 2197; q += blockDim.x) {
-    const int i = q / 169, j = (q / 13) % 13, l = q % 13;
-    ph[q] = phi[((int64_t)((bx - 2 + i) & mask) * M + ((by - 2 + j) & mask)) * M + ((bz - 2 + l) & mask)];
+  if (bz >= 8 && bz + 16 <= M) {
+    using V = typename Vec16<R>::T;
+    constexpr int N = Vec16<R>::N, PER = 16 / N;  // vectors per row
+    for (int v = threadIdx.x; v < 169 * PER; v += blockDim.x) {
+      const int r = v / PER, q = v % PER;
+      const int i = r / 13, j = r % 13;
+      const int64_t row = ((int64_t)((bx - 2 + i) & mask) * M + ((by - 2 + j) & mask)) * M;
+      reinterpret_cast<V*>(ph + r * 16)[q] = reinterpret_cast<const V*>(phi + row + bz - 4)[q];
+    }
+  } else {
+    for (int v = threadIdx.x; v < 169 * 16; v += blockDim.x) {
+      const int r = v >> 4, z = v & 15;
+      const int i = r / 13, j = r % 13;
+      ph[v] = phi[((int64_t)((bx - 2 + i) & mask) * M + ((by - 2 + j) & mask)) * M + ((bz - 4 + z) & mask)];
+    }
   }
   __syncthreads();
-  for (int q = threadIdx.x; q < 729; q += blockDim.x) {
-    const int i = q / 81 + 2, j = (q / 9) % 9 + 2, l = q % 9 + 2;
-    auto P = [&](int x, int y, int z) -> R { return ph[(x * 13 + y) * 13 + z]; };
-    gr[q] = (R)8 * (P(i + 1, j, l) - P(i - 1, j, l)) - (P(i + 2, j, l) - P(i - 2, j, l));
-    gr[729 + q] = (R)8 * (P(i, j + 1, l) - P(i, j - 1, l)) - (P(i, j + 2, l) - P(i, j - 2, l));
-    gr[1458 + q] = (R)8 * (P(i, j, l + 1) - P(i, j, l - 1)) - (P(i, j, l + 2) - P(i, j, l - 2));
+  const bool fly = p1 - p0 < kFlyMax;  // uniform across the block
+  if (!fly) {
+    for (int q = threadIdx.x; q < 729; q += blockDim.x) {
+      R gx, gy, gz;
+      grad_at(ph, q / 81, (q / 9) % 9, q % 9, gx, gy, gz);
+      gr[q] = gx;
+      gr[729 + q] = gy;
+      gr[1458 + q] = gz;
+    }
+    __syncthreads();
   }
-  __syncthreads();
   for (int64_t i = p0 + threadIdx.x; i < p1; i += blockDim.x) {
     uint64_t sx = (uint64_t)u[i] * (uint64_t)M, sy = (uint64_t)u[cap + i] * (uint64_t)M,
              sz = (uint64_t)u[2 * cap + i] * (uint64_t)M;
@@ -223,10 +340,18 @@ __global__ void __launch_bounds__(256) k_pm_interp_tile(const int32_t* __restric
     for (int o = 0; o < 8; ++o) {
       int ox = (o >> 2) & 1, oy = (o >> 1) & 1, oz = o & 1;
       R w = (ox ? fx : (R)1 - fx) * (oy ? fy : (R)1 - fy) * (oz ? fz : (R)1 - fz);
-      const int q = ((cx + ox) * 9 + (cy + oy)) * 9 + (cz + oz);
-      ax -= w * gr[q];
-      ay -= w * gr[729 + q];
-      az -= w * gr[1458 + q];
+      R gx, gy, gz;
+      if (fly) {
+        grad_at(ph, cx + ox, cy + oy, cz + oz, gx, gy, gz);
+      } else {
+        const int q = ((cx + ox) * 9 + (cy + oy)) * 9 + (cz + oz);
+        gx = gr[q];
+        gy = gr[729 + q];
+        gz = gr[1458 + q];
+      }
+      ax -= w * gx;
+      ay -= w * gy;
+      az -= w * gz;
     }
     g[i] = ax * inv12dx;
     g[cap + i] = ay * inv12dx;
@@ -236,7 +361,17 @@ __global__ void __launch_bounds__(256) k_pm_interp_tile(const int32_t* __restric
 
 // the deposit reads the depth-m cell table the tree build wrote for the same keys
 template <class R>
+void pm_smem_attributes() {
+  static bool done = false;  // once per process and type (the attribute is per function)
+  if (done) return;
+  cudaFuncSetAttribute(k_cic_gather<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gather_smem<R>());
+  cudaFuncSetAttribute(k_cic_gather<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gather_smem<R>());
+  done = true;
+}
+
+template <class R>
 void pm_deposit(dzs_ctx* c) {
+  pm_smem_attributes<R>();
   Buffers& B = c->B;
   const int M = c->M;
   const int64_t m3 = (int64_t)M * M * M;
@@ -246,8 +381,8 @@ void pm_deposit(dzs_ctx* c) {
     // mesh cells are the depth-m Morton cells of the tree's table
     const int sh = 3 * (kMaxLevel - c->logM);
     k_cic_cellw<R><<<grid_for(c->N0), kThreads, 0, c->stream>>>(B.n, c->cap, B.key, sh, B.u, B.k, M, (R*)B.cicw);
-    k_cic_gather<R><<<(unsigned)(m3 / 512), 256, 0, c->stream>>>(B.cell_start, B.n, c->cap, (const R*)B.cicw, M,
-                                                                 0, (R*)B.rho, inv_nbar);
+    k_cic_gather<R, true><<<(unsigned)(m3 / 512), 256, gather_smem<R>(), c->stream>>>(
+        B.cell_start, B.n, (const R*)B.cicw, M, (R*)B.rho, inv_nbar);
     return;
   }
   // M = 3 2^a: sort the particles by row-major mesh cell (scratch: key2 and
@@ -260,8 +395,8 @@ void pm_deposit(dzs_ctx* c) {
   launch_sort_keys(c, ka, kb, va, vb, 4);  // M^3 < 2^32
   k_cell_start<<<grid_for(c->N0 + 1), kThreads, 0, c->stream>>>(B.n, ka, 0, m3, B.cell_start);
   k_cic_cellw_perm<R><<<grid_for(c->N0), kThreads, 0, c->stream>>>(B.n, c->cap, ka, va, B.u, B.k, M, (R*)B.cicw);
-  k_cic_gather<R><<<(unsigned)(m3 / 512), 256, 0, c->stream>>>(B.cell_start, B.n, c->cap, (const R*)B.cicw, M, 1,
-                                                               (R*)B.rho, inv_nbar);
+  k_cic_gather<R, false><<<(unsigned)(m3 / 512), 256, gather_smem<R>(), c->stream>>>(
+      B.cell_start, B.n, (const R*)B.cicw, M, (R*)B.rho, inv_nbar);
 }
 
 template <class R>
@@ -286,7 +421,7 @@ void pm_interp(dzs_ctx* c) {
     return;
   }
   const int64_t tiles = (int64_t)(M / 8) * (M / 8) * (M / 8);
-  const size_t sm = (2197 + 3 * 729) * sizeof(R);
+  const size_t sm = (169 * 16 + 3 * 729) * sizeof(R);
   k_pm_interp_tile<R><<<(unsigned)tiles, 256, sm, c->stream>>>(B.cell_start, c->cap, B.u, (const R*)B.phi, M,
                                                                inv12dx, (R*)B.g);
 }
