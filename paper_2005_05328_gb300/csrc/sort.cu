@@ -24,9 +24,16 @@ __global__ void k_hist(const uint64_t* __restrict__ key, const int32_t* __restri
   __syncthreads();
   const int64_t n = *d_n;
   int64_t base = (int64_t)blockIdx.x * kTile;
+  uint64_t kv[kItems];  // all loads in flight before the first count
+#pragma unroll
   for (int s = 0; s < kItems; ++s) {
     int64_t i = base + s * kSortThreads + threadIdx.x;
-    if (i < n) atomicAdd(&cnt[(key[i] >> shift) & 0xff], 1u);
+    kv[s] = i < n ? key[i] : 0ull;
+  }
+#pragma unroll
+  for (int s = 0; s < kItems; ++s) {
+    int64_t i = base + s * kSortThreads + threadIdx.x;
+    if (i < n) atomicAdd(&cnt[(kv[s] >> shift) & 0xff], 1u);
   }
   __syncthreads();
   hist[threadIdx.x * nb + blockIdx.x] = cnt[threadIdx.x];
@@ -78,32 +85,42 @@ __global__ void k_scatter(const uint64_t* __restrict__ kin, const uint32_t* __re
   int64_t base = (int64_t)blockIdx.x * kTile;
   if (base >= n) return;
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-  // digit bases: exclusive scan of the 256 row totals (thread t owns digit t)
+  // the tile's keys and values, all loads in flight before any waiting
+  uint64_t kreg[kItems];
+  uint32_t vreg[kItems];
+#pragma unroll
+  for (int s = 0; s < kItems; ++s) {
+    const int64_t i = base + s * kSortThreads + t;
+    kreg[s] = i < n ? kin[i] : 0ull;
+    vreg[s] = i < n ? (identity_values ? (uint32_t)i : vin[i]) : 0u;
+  }
+  // digit bases: exclusive scan of the 256 row totals (thread t owns digit t):
+  // warp scans, then a scan of the 8 warp totals
   {
-    __shared__ uint32_t tot[kDigits];
-    tot[t] = rowtot[t];
-    __syncthreads();
-    if (t == 0) {
-      uint32_t s = 0;
-      for (int d = 0; d < kDigits; ++d) {
-        uint32_t v = tot[d];
-        tot[d] = s;
-        s += v;
-      }
+    __shared__ uint32_t wtot[kSortThreads / 32];
+    const uint32_t v = rowtot[t];
+    uint32_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
     }
+    if (lane == 31) wtot[w] = inc;
     __syncthreads();
-    gbase[t] = tot[t] + hist[(int64_t)t * nb + blockIdx.x];
+    uint32_t before = 0;
+    for (int q = 0; q < w; ++q) before += wtot[q];
+    gbase[t] = before + inc - v + hist[(int64_t)t * nb + blockIdx.x];
     run[t] = 0;
   }
-  __syncthreads();
   const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
   for (int s = 0; s < kItems; ++s) {
     for (int q = 0; q < kSortThreads / 32; ++q) wcnt[q][t] = 0;
     __syncthreads();
     int64_t i = base + s * kSortThreads + t;
     bool valid = i < n;
-    uint64_t kv = valid ? kin[i] : 0ull;
-    uint32_t vv = valid ? (identity_values ? (uint32_t)i : vin[i]) : 0u;
+    uint64_t kv = kreg[s];
+    uint32_t vv = vreg[s];
     int d = valid ? (int)((kv >> shift) & 0xff) : kDigits;  // invalid items group apart
     unsigned peers = __match_any_sync(0xffffffffu, d);
     int rank_w = __popc(peers & lt);
