@@ -33,9 +33,9 @@ UNIT = "particle-steps/s"
 # nominal FP32 pipe: 152 SMs x 128 lanes x 2 flop (FMA) x 2.07 GHz max SM clock
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # FP32 arithmetic of one pair evaluation of the walk (FMA = 2; rsqrt, exp2 = 1):
-# r^2 6, rsqrt 1, r 1, r^-3 2, x 1, t 2, split polynomial 22, exp 4, force 2,
-# accumulate 6 ("walk roofline")
-FLOP_PER_PAIR = 47
+# r^2 6, rsqrt 1, r 1, r^-3 2, t 2, split polynomial 22, exp 3 (r^2 scale, exp2,
+# times Q), force 2, accumulate 6 ("walk roofline")
+FLOP_PER_PAIR = 45
 
 # algorithmic HBM bytes per step of the streaming stages, FP32 state
 # (u 12 B, p 12 B, g 12 B, k 4 B, id 4 B, flags 1 B per particle; mesh M^3);
@@ -55,8 +55,8 @@ STAGE_BYTES = {
 # DRAM bytes (read + write) of one k_walk launch from an ncu capture (step 41 of
 # the bench run, z ~ 4) and the walk source it was taken on: reported as
 # roofline traffic only while the source is unchanged
-WALK_TRAFFIC_BYTES = 174.834e6 + 35.567e6
-WALK_TRAFFIC_SRC = "7719c5770be3f846"
+WALK_TRAFFIC_BYTES = 172.605e6 + 35.825e6
+WALK_TRAFFIC_SRC = "86812881f7ef2e16"
 
 # serving sample (Poisson stream of mock requests, sizes 32^3 .. 256^3)
 SERVE_RATE = 4.0

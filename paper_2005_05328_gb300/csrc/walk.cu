@@ -5,7 +5,16 @@
 //
 // One warp per walk group (a node with <= G particles whose parent holds more,
 // or a leaf).  The warp walks the tree against the group's cube with a
-// shared-memory stack, up to 32 nodes per round (one per lane):
+// shared-memory stack, up to 32 nodes per round (one per lane), starting from
+// the frontier depth f: the deepest depth above which no node can be accepted
+// (a node of side l whose cube is within r_cut of the group cube has its COM
+// within r_cut + sqrt(3) l, which opens it while that is <= l / theta), and
+// whose cells are at least r_cut wide.  From the root the walk would only open
+// or skip nodes above f, so it starts instead from the depth-f nodes of the 27
+// cells around the group's depth-f cell (or the shallower leaves covering
+// them, each once): the same nodes are tested and the same interaction set is
+// built, without the first rounds of the descent.  Groups above depth f start
+// at the root.  Per node:
 //   skip   the node's cube is farther than r_cut from the group cube;
 //   open   the cubes touch, or l_n >= theta d(COM_n, group cube);
 //   accept otherwise: the monopole (COM, mass, softening) joins the list.
@@ -70,6 +79,8 @@ template <class R>
 struct WalkConst {
   R rcut2;   // (r_cut / s)^2
   R inv2rs;  // s / (2 r_s)
+  R tcoef;   // (s / 2 r_s) * 2 / x_max (polynomial variable t = r tcoef - 1)
+  R nl2;     // -log2(e) (s / 2 r_s)^2
   R gm0;     // G m0 / s^2
   R kick;    // closing kick factor
   uint64_t skip_d2;                 // not skipped iff cube gap^2 <= skip_d2
@@ -80,6 +91,8 @@ struct WalkConst {
   int close;
   int tree;
   int poly;  // FP32: use the fitted split polynomial (x_max <= 2.5)
+  int front;                  // frontier depth f (0: start at the root)
+  const int32_t* ftab;        // [2^f]^3 row-major: node of each depth-f cell, -1 if empty
 };
 
 __device__ __forceinline__ uint64_t exact_d2(const uint32_t (&v)[3]) {
@@ -104,6 +117,13 @@ __device__ __forceinline__ float split_factor(float x, int poly) {
     return __expf(-x * x) * q;
   }
   return erfcf(x) + 1.1283791670955126f * x * __expf(-x * x);
+}
+
+// exp(-x^2) = 2^(r^2 * nl2) with nl2 = -log2(e) (s / 2 r_s)^2: one multiply from r^2
+__device__ __forceinline__ float ex2_approx(float v) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(v));
+  return y;
 }
 
 __device__ __forceinline__ double split_factor(double x, int) {
@@ -132,7 +152,17 @@ __device__ __forceinline__ void pair(const Entry<R>& E, R he, uint32_t xi, uint3
     inv_and_r(r2, r, ir);
     R h = he > hi ? he : hi;
     R fac = (r >= h) ? ir * ir * ir : spline_fac(r, h);
-    R f = E.m * fac * split_factor(r * C.inv2rs, C.poly);
+    R sfac;
+    if (sizeof(R) == 4 && C.poly) {
+      const float t = fmaf((float)r, (float)C.tcoef, -1.0f);
+      float q = kSplitPoly[11];
+#pragma unroll
+      for (int i = 10; i >= 0; --i) q = fmaf(q, t, kSplitPoly[i]);
+      sfac = (R)(ex2_approx((float)r2 * (float)C.nl2) * q);
+    } else {
+      sfac = split_factor(r * C.inv2rs, C.poly);
+    }
+    R f = E.m * fac * sfac;
     ax += f * dx;
     ay += f * dy;
     az += f * dz;
@@ -193,6 +223,27 @@ __global__ void k_walk_prep(const int32_t* __restrict__ d_n, int64_t cap, const 
   }
 }
 
+// frontier table: every node of depth f, and every leaf above it, writes its
+// index into the depth-f cells it covers (cells partition the box: no conflicts)
+__global__ void k_front_fill(const int32_t* __restrict__ lvl, const Node* __restrict__ nodes, int f,
+                             int32_t* __restrict__ ftab) {
+  int64_t nf = 0;
+  for (int j = 0; j <= f; ++j) nf += lvl[j];
+  const int D = 1 << f;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nf; t += (int64_t)gridDim.x * blockDim.x) {
+    const Node nd = nodes[t];
+    const int j = (int)(nd.meta & 0xff);
+    if (j < f && nd.child >= 0) continue;  // internal above f: its depth-f descendants write
+    const int span = 1 << (f - j);
+    const uint32_t h = j == 0 ? 0x80000000u : (1u << (31 - j));
+    const int x0 = (int)((nd.cx - h) >> (32 - f)), y0 = (int)((nd.cy - h) >> (32 - f)),
+              z0 = (int)((nd.cz - h) >> (32 - f));
+    for (int a = 0; a < span; ++a)
+      for (int b = 0; b < span; ++b)
+        for (int c = 0; c < span; ++c) ftab[((int64_t)(x0 + a) * D + (y0 + b)) * D + (z0 + c)] = (int32_t)t;
+  }
+}
+
 template <class R>
 __global__ void __launch_bounds__(kWarps * 32) k_walk(
     const int32_t* __restrict__ groups, const uint64_t* __restrict__ counters, unsigned int* __restrict__ next,
@@ -234,8 +285,27 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(
       R ax = 0, ay = 0, az = 0;
       if (C.tree) {
         int top = 0, len = 0;
-        if (lane == 0) sm.stack[w][0] = 0;
-        top = 1;
+        if (C.front > 0 && glevel >= C.front) {
+          // the nodes of the 27 cells around the group's depth-f cell, each once
+          const int f = C.front, D = 1 << f;
+          int ni = -1;
+          if (lane < 27) {
+            const int x = (int)((gn.cx >> (32 - f)) + lane / 9 + D - 1) & (D - 1);
+            const int y = (int)((gn.cy >> (32 - f)) + (lane / 3) % 3 + D - 1) & (D - 1);
+            const int z = (int)((gn.cz >> (32 - f)) + lane % 3 + D - 1) & (D - 1);
+            ni = C.ftab[((int64_t)x * D + y) * D + z];
+          }
+          for (int q = 0; q < 26; ++q) {
+            const int o = __shfl_sync(0xffffffffu, ni, q);
+            if (q < lane && o == ni) ni = -1;
+          }
+          const unsigned fm = __ballot_sync(0xffffffffu, ni >= 0);
+          if (ni >= 0) sm.stack[w][__popc(fm & lt)] = ni;
+          top = __popc(fm);
+        } else {
+          if (lane == 0) sm.stack[w][0] = 0;
+          top = 1;
+        }
         __syncwarp();
         while (top > 0) {
           const int npop = top < 32 ? top : 32;
@@ -425,6 +495,8 @@ void walk_impl(dzs_ctx* c, bool tree, bool close_kick, int step) {
   WalkConst<R> C;
   C.rcut2 = (R)((c->rcut / s) * (c->rcut / s));
   C.inv2rs = (R)(s / (2.0 * c->rs));
+  C.tcoef = (R)(s / (2.0 * c->rs) * (2.0 / (double)kSplitXMax));
+  C.nl2 = (R)(-1.4426950408889634 * (s / (2.0 * c->rs)) * (s / (2.0 * c->rs)));
   C.gm0 = (R)(c->gm0 / (s * s));
   C.kick = close_kick ? (R)c->T.kick2[step] : (R)0;
   C.skip_d2 = c->walk_skip_d2;
@@ -443,12 +515,34 @@ void walk_impl(dzs_ctx* c, bool tree, bool close_kick, int step) {
   C.close = close_kick ? 1 : 0;
   C.tree = tree ? 1 : 0;
   C.poly = (c->P.rcut_rs / 2.0 <= (double)kSplitXMax) ? 1 : 0;
+  // frontier depth: every depth above it never accepts (a non-skipped node's
+  // COM distance is at most sqrt(skip_d2) + sqrt(3) l, and that opens it), and
+  // its cells are wider than r_cut (cells beyond the 27 neighbours are skipped)
+  C.front = 0;
+  C.ftab = c->B.iscan;  // scratch: the tree's tile counts are no longer needed
+  const int64_t ftab_cap = 2 * c->cap + 64;
+  for (int f = 1; f <= 7 && ((int64_t)1 << (3 * f)) <= ftab_cap; ++f) {
+    const double lf = std::ldexp(1.0, 32 - f), lp = std::ldexp(1.0, 33 - f);
+    const double reach = std::sqrt((double)C.skip_d2) + 1.7320508075688772 * lp;
+    // (a saturated threshold opens at every representable distance)
+    const bool never = C.open_d2[f - 1] == ~0ull || reach * reach * (1.0 + 1e-9) <= (double)C.open_d2[f - 1];
+    const bool wide = lf * lf > (double)C.skip_d2 * (1.0 + 1e-9);
+    if (!(never && wide)) break;
+    C.front = f;
+  }
   Entry<R>* pm = (Entry<R>*)c->B.wpm;
   R* ph = (R*)c->B.wph;
   R* nh = (R*)c->B.wnh;
   k_walk_prep<R><<<grid_for(c->node_cap), kThreads, 0, c->stream>>>(c->B.n, c->cap, c->B.u, c->B.k, c->B.lvl_count,
                                                                      c->B.nodes, pm, ph, nh, C.gm0,
                                                                      (R)(2.8 * c->eps0 / s));
+  if (C.front > 0 && tree) {
+    const int64_t cells = (int64_t)1 << (3 * C.front);
+    c->launches += 1;
+    cudaMemsetAsync(c->B.iscan, 0xff, sizeof(int32_t) * cells, c->stream);
+    k_front_fill<<<grid_for(cells, kThreads, 152 * 4), kThreads, 0, c->stream>>>(c->B.lvl_count, c->B.nodes, C.front,
+                                                                               c->B.iscan);
+  }
   size_t sm = sizeof(WalkSmem<R>);
   static bool attr_done[2] = {false, false};
   if (!attr_done[sizeof(R) == 8]) {
