@@ -133,6 +133,17 @@ struct Split {
   static constexpr int N1 = N / N2;
 };
 
+// shared-memory slot of element row `row` of column `col` in a block of W
+// columns: for W a power of two the column index is XOR-swizzled with the row
+// (the transposing loads of the Z passes, consecutive rows of one column, then
+// fall on distinct banks; consecutive columns of one row stay a permutation of
+// one row), otherwise rows are padded to W + 1
+__device__ __forceinline__ int sidx(int row, int col, int W) {
+  return (W & (W - 1)) == 0 ? row * W + (col ^ (row & (W - 1))) : row * (W + 1) + col;
+}
+
+__host__ __device__ constexpr int srows(int W) { return (W & (W - 1)) == 0 ? W : W + 1; }
+
 // ---- generic four-step pieces on one column held in shared memory
 // step A: thread (col, j2) transforms x[j1 N2 + j2] over j1, twiddles, and
 // writes Y[k1 N2 + j2] back into the same column
@@ -142,12 +153,12 @@ __device__ __forceinline__ void stepA_smem(cplx<R>* buf, int W, int col, int j2,
   constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
   cplx<R> a[N1];
 #pragma unroll
-  for (int j1 = 0; j1 < N1; ++j1) a[j1] = buf[(j1 * N2 + j2) * W + col];
+  for (int j1 = 0; j1 < N1; ++j1) a[j1] = buf[sidx((j1 * N2 + j2), col, W)];
   reg_fft<R, N1>(a, inv);
 #pragma unroll
   for (int k1 = 0; k1 < N1; ++k1) a[k1] = cmul(a[k1], twn(tw, j2 * k1, N, inv));
 #pragma unroll
-  for (int k1 = 0; k1 < N1; ++k1) buf[(k1 * N2 + j2) * W + col] = a[k1];
+  for (int k1 = 0; k1 < N1; ++k1) buf[sidx((k1 * N2 + j2), col, W)] = a[k1];
 }
 
 // step B: thread (col, k1) transforms Y[k1 N2 + j2] over j2; result element
@@ -157,7 +168,7 @@ __device__ __forceinline__ void stepB_smem(const cplx<R>* buf, int W, int col, i
                                            bool inv) {
   constexpr int N2 = Split<N>::N2;
 #pragma unroll
-  for (int j2 = 0; j2 < N2; ++j2) b[j2] = buf[(k1 * N2 + j2) * W + col];
+  for (int j2 = 0; j2 < N2; ++j2) b[j2] = buf[sidx((k1 * N2 + j2), col, W)];
   reg_fft<R, N2>(b, inv);
 }
 
@@ -169,13 +180,13 @@ __global__ void k_fft_z_r2c(const R* __restrict__ in, cplx<R>* __restrict__ out,
   extern __shared__ unsigned char smem_raw[];
   cplx<R>* buf = reinterpret_cast<cplx<R>*>(smem_raw);
   const int64_t p0 = (int64_t)blockIdx.x * W;
-  // coalesced load: element e of pair col at buf[e * W + col]
+  // coalesced load: element e of pair col at buf[sidx(e, col, W)]
   for (int q = threadIdx.x; q < N * W; q += blockDim.x) {
     int col = q / N, e = q % N;
     int64_t pr = p0 + col;
     cplx<R> v = {0, 0};
     if (pr < npairs) v = {in[(2 * pr) * N + e], in[(2 * pr + 1) * N + e]};
-    buf[e * W + col] = v;
+    buf[sidx(e, col, W)] = v;
   }
   __syncthreads();
   const int col = threadIdx.x % W, r = threadIdx.x / W;
@@ -186,7 +197,7 @@ __global__ void k_fft_z_r2c(const R* __restrict__ in, cplx<R>* __restrict__ out,
   __syncthreads();
   if (r < N1) {
 #pragma unroll
-    for (int k2 = 0; k2 < N2; ++k2) buf[(r + N1 * k2) * W + col] = b[k2];
+    for (int k2 = 0; k2 < N2; ++k2) buf[sidx((r + N1 * k2), col, W)] = b[k2];
   }
   __syncthreads();
   // unpack: X_a = (Z_k + conj Z_-k) / 2,  X_b = (Z_k - conj Z_-k) / (2 i)
@@ -194,7 +205,7 @@ __global__ void k_fft_z_r2c(const R* __restrict__ in, cplx<R>* __restrict__ out,
     int c = q / HN, k = q % HN;
     int64_t pr = p0 + c;
     if (pr >= npairs) continue;
-    cplx<R> z = buf[(k % N) * W + c], zc = buf[((N - k) % N) * W + c];
+    cplx<R> z = buf[sidx((k % N), c, W)], zc = buf[sidx(((N - k) % N), c, W)];
     out[(2 * pr) * HN + k] = {(R)0.5 * (z.x + zc.x), (R)0.5 * (z.y - zc.y)};
     out[(2 * pr + 1) * HN + k] = {(R)0.5 * (z.y + zc.y), (R)-0.5 * (z.x - zc.x)};
   }
@@ -225,7 +236,7 @@ __global__ void k_fft_z_c2r(const cplx<R>* __restrict__ in, R* __restrict__ out,
       }
       z = {a.x - b.y, a.y + b.x};  // a + i b
     }
-    buf[k * W + col] = z;
+    buf[sidx(k, col, W)] = z;
   }
   __syncthreads();
   const int col = threadIdx.x % W, r = threadIdx.x / W;
@@ -236,14 +247,14 @@ __global__ void k_fft_z_c2r(const cplx<R>* __restrict__ in, R* __restrict__ out,
   __syncthreads();
   if (r < N1) {
 #pragma unroll
-    for (int k2 = 0; k2 < N2; ++k2) buf[(r + N1 * k2) * W + col] = b[k2];
+    for (int k2 = 0; k2 < N2; ++k2) buf[sidx((r + N1 * k2), col, W)] = b[k2];
   }
   __syncthreads();
   for (int q = threadIdx.x; q < N * W; q += blockDim.x) {
     int c = q / N, e = q % N;
     int64_t pr = p0 + c;
     if (pr >= npairs) continue;
-    cplx<R> z = buf[e * W + c];
+    cplx<R> z = buf[sidx(e, c, W)];
     out[(2 * pr) * N + e] = z.x;
     out[(2 * pr + 1) * N + e] = z.y;
   }
@@ -273,7 +284,7 @@ __global__ void k_fft_cols(cplx<R>* __restrict__ spec, int W, int axis, int mode
     for (int j1 = 0; j1 < N1; ++j1) a[j1] = valid ? spec[base + (j1 * N2 + r) * es + kz0 + col] : cplx<R>{0, 0};
     reg_fft<R, N1>(a, inv);
 #pragma unroll
-    for (int k1 = 0; k1 < N1; ++k1) buf[(k1 * N2 + r) * W + col] = cmul(a[k1], twn(tw, r * k1, N, inv));
+    for (int k1 = 0; k1 < N1; ++k1) buf[sidx((k1 * N2 + r), col, W)] = cmul(a[k1], twn(tw, r * k1, N, inv));
   }
   __syncthreads();
   cplx<R> b[N2];
@@ -310,13 +321,13 @@ __global__ void k_fft_cols(cplx<R>* __restrict__ spec, int W, int axis, int mode
   if (r < N1) {
     reg_fft<R, N2>(b, true);
 #pragma unroll
-    for (int k2 = 0; k2 < N2; ++k2) buf[(k2 * N1 + r) * W + col] = cmul(b[k2], twn(tw, r * k2, N, true));
+    for (int k2 = 0; k2 < N2; ++k2) buf[sidx((k2 * N1 + r), col, W)] = cmul(b[k2], twn(tw, r * k2, N, true));
   }
   __syncthreads();
   if (r < N2) {
     cplx<R> a[N1];
 #pragma unroll
-    for (int j = 0; j < N1; ++j) a[j] = buf[(r * N1 + j) * W + col];
+    for (int j = 0; j < N1; ++j) a[j] = buf[sidx((r * N1 + j), col, W)];
     reg_fft<R, N1>(a, true);
     if (valid) {
 #pragma unroll
@@ -327,9 +338,9 @@ __global__ void k_fft_cols(cplx<R>* __restrict__ spec, int W, int axis, int mode
 
 template <class R, int N>
 int cols_per_block() {
-  // W * N1 threads per block, at most 256; shared memory W * N * sizeof(cplx)
+  // W * N1 threads per block, at most 256; shared memory srows(W) * N * sizeof(cplx)
   int w = 256 / Split<N>::N1;
-  while (w > 1 && (size_t)w * N * sizeof(cplx<R>) > 48 * 1024) w >>= 1;
+  while (w > 1 && (size_t)srows(w) * N * sizeof(cplx<R>) > 48 * 1024) w >>= 1;
   return w;
 }
 
@@ -337,7 +348,7 @@ template <class R, int N>
 void launch_r2c_zy(dzs_ctx* c, const R* in, cplx<R>* out, const cplx<R>* tw, bool do_x) {
   const int W = cols_per_block<R, N>();
   const int threads = W * Split<N>::N1;
-  const size_t sm = (size_t)N * W * sizeof(cplx<R>);
+  const size_t sm = (size_t)N * srows(W) * sizeof(cplx<R>);
   const int64_t npairs = (int64_t)N * N / 2;
   k_fft_z_r2c<R, N><<<(unsigned)((npairs + W - 1) / W), threads, sm, c->stream>>>(in, out, W, npairs, tw);
   const int ncb = (N / 2 + 1 + W - 1) / W;
@@ -349,7 +360,7 @@ template <class R, int N>
 void launch_c2r(dzs_ctx* c, cplx<R>* in, R* out, const cplx<R>* tw, const R* green, R gfac) {
   const int W = cols_per_block<R, N>();
   const int threads = W * Split<N>::N1;
-  const size_t sm = (size_t)N * W * sizeof(cplx<R>);
+  const size_t sm = (size_t)N * srows(W) * sizeof(cplx<R>);
   const int64_t npairs = (int64_t)N * N / 2;
   const int ncb = (N / 2 + 1 + W - 1) / W;
   k_fft_cols<R, N><<<N * ncb, threads, sm, c->stream>>>(in, W, 0, green ? 2 : 1, tw, green, gfac);

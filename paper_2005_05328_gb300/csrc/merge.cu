@@ -212,6 +212,37 @@ __device__ __forceinline__ int64_t lower_bound_key(const uint64_t* __restrict__ 
 }
 
 // mend[i]: end of the merged run if i leads one, -1 if i is merged away, 0 if kept
+// first index s <= i with key[s] >= x, given key[i] >= x: exponential steps
+// down from i, then a binary search of the last step (cost ~2 log2(i - s))
+__device__ __forceinline__ int64_t gallop_down(const uint64_t* __restrict__ key, int64_t i, uint64_t x) {
+  int64_t hi = i, lo = 0;
+  for (int64_t step = 1;; step <<= 1) {
+    const int64_t p = i - step;
+    if (p < 0) break;
+    if (key[p] < x) {
+      lo = p + 1;
+      break;
+    }
+    hi = p;
+  }
+  return lower_bound_key(key, lo, hi + 1, x);
+}
+
+// first index >= i1 with key >= x (or n), given key[i1 - 1] < x
+__device__ __forceinline__ int64_t gallop_up(const uint64_t* __restrict__ key, int64_t i1, int64_t n, uint64_t x) {
+  int64_t lo = i1, hi = n;
+  for (int64_t step = 1;; step <<= 1) {
+    const int64_t p = i1 - 1 + step;
+    if (p >= n) break;
+    if (key[p] >= x) {
+      hi = p;
+      break;
+    }
+    lo = p + 1;
+  }
+  return lower_bound_key(key, lo, hi, x);
+}
+
 __global__ void k_merge_mark(const int32_t* __restrict__ d_n, int64_t cap, const uint64_t* __restrict__ key,
                              const uint32_t* __restrict__ u, const uint64_t* __restrict__ pre,
                              int32_t* __restrict__ mend, int32_t* __restrict__ keep, MergeParams mp) {
@@ -230,16 +261,25 @@ __global__ void k_merge_mark(const int32_t* __restrict__ d_n, int64_t cap, const
     if (mp.filter) cand = dist2_obs(u[i], u[cap + i], u[2 * cap + i]) > mp.rb2;
     if (cand) {
       uint64_t ki = key[i];
+      // candidate cells start at depth jmin: its bounds by galloping out from i
+      // (the coarser cells only contain it), deeper ones inside the previous
+      const int j0 = mp.jmin > 1 ? mp.jmin : 1;
       int64_t lo = 0, hi = n;
-      for (int j = 1; j <= kMaxLevel; ++j) {
+      for (int j = j0; j <= kMaxLevel; ++j) {
         int sh = 3 * (kMaxLevel - j);
         uint64_t cell = (ki >> sh) << sh;
-        int64_t s = lower_bound_key(key, lo, i + 1, cell);
-        int64_t e = lower_bound_key(key, i + 1, hi, cell + (1ull << sh));
+        int64_t s, e;
+        if (j == j0) {
+          s = gallop_down(key, i, cell);
+          e = gallop_up(key, i + 1, n, cell + (1ull << sh));
+        } else {
+          s = lower_bound_key(key, lo, i + 1, cell);
+          e = lower_bound_key(key, i + 1, hi, cell + (1ull << sh));
+        }
         lo = s;
         hi = e;
         if (e - s < 2) break;  // no finer cell holds two particles
-        if (j < mp.jmin || (mp.criterion == DZS_CRIT_GEOMETRIC && mp.thr[j] == ~0ull)) continue;
+        if (mp.criterion == DZS_CRIT_GEOMETRIC && mp.thr[j] == ~0ull) continue;
         uint64_t K = PK[e] - PK[s];
         uint64_t d2 = 0;
         for (int ax = 0; ax < 3; ++ax) {
