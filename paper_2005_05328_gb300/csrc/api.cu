@@ -95,7 +95,7 @@ struct Plan {
     node_cap = 2 * cap + 1024;
     m3 = (int64_t)P.mesh * P.mesh * P.mesh;
     nspec = (int64_t)P.mesh * P.mesh * (P.mesh / 2 + 1);
-    nb = (cap + 2047) / 2048;
+    nb = (cap + 1023) / 1024;  // digit-histogram tiles: enough for sort tiles of >= 1024 keys
     nchunks = (cap + 1024) / 1024 + 1;
     ring = P.lc_capacity ? (int64_t)P.lc_capacity : cap;
     rsz = P.precision == DZS_FP64 ? 8 : 4;

@@ -78,12 +78,16 @@ __global__ void k_scatter(const uint64_t* __restrict__ kin, const uint32_t* __re
                           uint64_t* __restrict__ kout, uint32_t* __restrict__ vout,
                           const int32_t* __restrict__ d_n, int shift, const uint32_t* __restrict__ hist,
                           int nb, const uint32_t* __restrict__ rowtot, bool identity_values) {
-  __shared__ uint32_t gbase[kDigits];
+  __shared__ uint32_t gbase[kDigits];  // output position of the tile's first key of each digit
+  __shared__ uint32_t lbase[kDigits];  // the same within the tile (tile sorted by digit)
   __shared__ uint32_t run[kDigits];
   __shared__ uint32_t wcnt[kSortThreads / 32][kDigits];
+  __shared__ uint64_t sk[kTile];       // the tile, stably sorted by digit
+  __shared__ uint32_t sv[kTile];
   const int64_t n = *d_n;
   int64_t base = (int64_t)blockIdx.x * kTile;
   if (base >= n) return;
+  const int tile_n = (int)(n - base < kTile ? n - base : kTile);
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   // the tile's keys and values, all loads in flight before any waiting
   uint64_t kreg[kItems];
@@ -94,22 +98,35 @@ __global__ void k_scatter(const uint64_t* __restrict__ kin, const uint32_t* __re
     kreg[s] = i < n ? kin[i] : 0ull;
     vreg[s] = i < n ? (identity_values ? (uint32_t)i : vin[i]) : 0u;
   }
-  // digit bases: exclusive scan of the 256 row totals (thread t owns digit t):
-  // warp scans, then a scan of the 8 warp totals
+  // digit bases: exclusive scans over the 256 digits (thread t owns digit t) of
+  // the row totals (global) and of this tile's counts (local); warp scans,
+  // then a scan of the 8 warp totals
   {
-    __shared__ uint32_t wtot[kSortThreads / 32];
-    const uint32_t v = rowtot[t];
-    uint32_t inc = v;
+    __shared__ uint32_t wtot[2][kSortThreads / 32];
+    const uint32_t h0 = hist[(int64_t)t * nb + blockIdx.x];
+    const uint32_t h1 = blockIdx.x + 1 < (unsigned)nb ? hist[(int64_t)t * nb + blockIdx.x + 1] : rowtot[t];
+    const uint32_t v = rowtot[t], c = h1 - h0;
+    uint32_t inc = v, incc = c;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-      if (lane >= o) inc += y;
+      const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o), yc = __shfl_up_sync(0xffffffffu, incc, o);
+      if (lane >= o) {
+        inc += y;
+        incc += yc;
+      }
     }
-    if (lane == 31) wtot[w] = inc;
+    if (lane == 31) {
+      wtot[0][w] = inc;
+      wtot[1][w] = incc;
+    }
     __syncthreads();
-    uint32_t before = 0;
-    for (int q = 0; q < w; ++q) before += wtot[q];
-    gbase[t] = before + inc - v + hist[(int64_t)t * nb + blockIdx.x];
+    uint32_t before = 0, beforec = 0;
+    for (int q = 0; q < w; ++q) {
+      before += wtot[0][q];
+      beforec += wtot[1][q];
+    }
+    gbase[t] = before + inc - v + h0;
+    lbase[t] = beforec + incc - c;
     run[t] = 0;
   }
   const unsigned lt = (1u << lane) - 1u;
@@ -137,11 +154,23 @@ __global__ void k_scatter(const uint64_t* __restrict__ kin, const uint32_t* __re
     }
     __syncthreads();
     if (valid) {
-      uint32_t pos = gbase[d] + wcnt[w][d] + (uint32_t)rank_w;
-      kout[pos] = kv;
-      vout[pos] = vv;
+      const uint32_t lp = lbase[d] + wcnt[w][d] + (uint32_t)rank_w;
+      if (lp < (uint32_t)kTile) {  // always, when the tile's histogram matches its keys
+        sk[lp] = kv;
+        sv[lp] = vv;
+      }
     }
-    __syncthreads();
+    __syncthreads();  // wcnt is read above and cleared at the top of the next round
+  }
+  // runs of one digit are contiguous in the tile and in the output: coalesced
+  for (int q = t; q < tile_n; q += kSortThreads) {
+    const uint64_t kv = sk[q];
+    const int d = (int)((kv >> shift) & 0xff);
+    const uint32_t pos = gbase[d] + (uint32_t)q - lbase[d];
+    if ((int64_t)pos < n) {
+      kout[pos] = kv;
+      vout[pos] = sv[q];
+    }
   }
 }
 
