@@ -140,17 +140,15 @@ __global__ void k_mesh_keys(const int32_t* __restrict__ d_n, int64_t cap, const 
 //      cells the tile's own 8^3 cells are one run of the table (513
 //      consecutive entries, coalesced) and only the 217 cells of the three
 //      lower halo planes are looked up one by one;
-//   2. the 8 weight sums of every non-empty cell (one 8-value record each)
-//      into shared memory, zeros for empty cells;
-//   3. each node adds its 8 cells in the fixed order o = 0..7 (empty cells
-//      add +0), so the mesh is deterministic.
+//   2. each node adds the corner weight sums of its 8 cells in the fixed
+//      order o = 0..7, read from the cells' records in global memory (L2;
+//      empty cells add +0), so the mesh is deterministic.
 template <class R, bool kMorton>
 __global__ void __launch_bounds__(256) k_cic_gather(const int32_t* __restrict__ start, const int32_t* __restrict__ d_n,
                                                     const R* __restrict__ W, int M, R* __restrict__ delta,
                                                     R inv_nbar) {
   extern __shared__ unsigned char cg_raw[];
-  R* wv = reinterpret_cast<R*>(cg_raw);                   // [8][729]
-  int32_t* first = reinterpret_cast<int32_t*>(wv + 8 * 729);  // [729] first particle, -1 empty
+  int32_t* first = reinterpret_cast<int32_t*>(cg_raw);  // [729] first particle, -1 empty
   int32_t* sb = first + 729;                               // [513] the tile's own bounds
   const int T = M >> 3;
   const int tile = blockIdx.x;
@@ -195,25 +193,6 @@ __global__ void __launch_bounds__(256) k_cic_gather(const int32_t* __restrict__ 
     }
   }
   __syncthreads();
-  using V = typename Vec16<R>::T;
-  constexpr int N = Vec16<R>::N;
-  for (int q = threadIdx.x; q < 729; q += blockDim.x) {
-    const int32_t f = first[q];
-    if (f >= 0) {
-      const V* src = reinterpret_cast<const V*>(W + 8 * (int64_t)f);
-#pragma unroll
-      for (int v = 0; v < 8 / N; ++v) {
-        const V x = src[v];
-        const R* xs = reinterpret_cast<const R*>(&x);
-#pragma unroll
-        for (int r = 0; r < N; ++r) wv[(v * N + r) * 729 + q] = xs[r];
-      }
-    } else {
-#pragma unroll
-      for (int o = 0; o < 8; ++o) wv[o * 729 + q] = (R)0;
-    }
-  }
-  __syncthreads();
   for (int t = threadIdx.x; t < 512; t += blockDim.x) {
     const int a = t >> 6, b = (t >> 3) & 7, c = t & 7;
     const int q0 = (a + 1) * 81 + (b + 1) * 9 + (c + 1);
@@ -221,7 +200,8 @@ __global__ void __launch_bounds__(256) k_cic_gather(const int32_t* __restrict__ 
 #pragma unroll
     for (int o = 0; o < 8; ++o) {
       const int ox = (o >> 2) & 1, oy = (o >> 1) & 1, oz = o & 1;
-      acc += wv[o * 729 + q0 - ox * 81 - oy * 9 - oz];
+      const int32_t f = first[q0 - ox * 81 - oy * 9 - oz];
+      acc += f >= 0 ? W[8 * (int64_t)f + o] : (R)0;
     }
     delta[((int64_t)(bx + a) * M + (by + b)) * M + (bz + c)] = acc * inv_nbar - (R)1;
   }
@@ -229,7 +209,7 @@ __global__ void __launch_bounds__(256) k_cic_gather(const int32_t* __restrict__ 
 
 template <class R>
 constexpr size_t gather_smem() {
-  return 8 * 729 * sizeof(R) + (729 + 513) * sizeof(int32_t);
+  return (729 + 513) * sizeof(int32_t);
 }
 
 // g = -grad phi at the particles for any mesh (used for M = 3 2^a): the
