@@ -23,11 +23,32 @@ namespace {
 
 __global__ void k_cell_start(const int32_t* __restrict__ d_n, const uint64_t* __restrict__ key, int sh,
                              int64_t ncell, int32_t* __restrict__ start) {
+  // particle i writes i into the cells after its predecessor's cell up to its
+  // own (i = n: up to the end); a lane fills a short run itself, the warp
+  // fills long runs (gaps of empty cells) together, coalesced
   const int64_t n = *d_n;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += (int64_t)gridDim.x * blockDim.x) {
-    int64_t ci = (i < n) ? (int64_t)(key[i] >> sh) : ncell;
-    int64_t cp = (i > 0) ? (int64_t)(key[i - 1] >> sh) : -1;
-    for (int64_t q = cp + 1; q <= ci; ++q) start[q] = (int32_t)i;
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t w0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; w0 <= n; w0 += stride) {
+    const int64_t i = w0 + lane;
+    int64_t lo = 0, hi = 0;  // cells [lo, hi) take the value i
+    if (i <= n) {
+      const int64_t ci = (i < n) ? (int64_t)(key[i] >> sh) : ncell;
+      const int64_t cp = (i > 0) ? (int64_t)(key[i - 1] >> sh) : -1;
+      lo = cp + 1;
+      hi = ci + 1;
+    }
+    const bool longrun = hi - lo > 32;
+    if (!longrun)
+      for (int64_t q = lo; q < hi; ++q) start[q] = (int32_t)i;
+    unsigned lm = __ballot_sync(0xffffffffu, longrun);
+    while (lm) {
+      const int src = __ffs(lm) - 1;
+      lm &= lm - 1;
+      const int64_t qlo = __shfl_sync(0xffffffffu, lo, src), qhi = __shfl_sync(0xffffffffu, hi, src);
+      const int32_t v = (int32_t)__shfl_sync(0xffffffffu, i, src);
+      for (int64_t q = qlo + lane; q < qhi; q += 32) start[q] = v;
+    }
   }
 }
 
