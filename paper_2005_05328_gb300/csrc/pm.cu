@@ -178,9 +178,13 @@ __global__ void __launch_bounds__(256) k_cic_gather(const int32_t* __restrict__ 
   const int32_t n = *d_n;
   auto clampb = [n](int32_t v) { return v < 0 ? 0 : (v > n ? n : v); };
   auto cell_of = [&](int i, int j, int l) -> int64_t {  // 9^3 coordinates (offset -1)
+    if (kMorton) {  // M = 2^m: periodic wrap by a mask
+      const uint32_t mk = (uint32_t)M - 1u;
+      return (int64_t)morton_cell((uint32_t)(bx + i - 1) & mk, (uint32_t)(by + j - 1) & mk, (uint32_t)(bz + l - 1) & mk);
+    }
     const uint32_t gx = (uint32_t)((bx + i - 1 + M) % M), gy = (uint32_t)((by + j - 1 + M) % M),
                    gz = (uint32_t)((bz + l - 1 + M) % M);
-    return kMorton ? (int64_t)morton_cell(gx, gy, gz) : ((int64_t)gx * M + gy) * M + gz;
+    return ((int64_t)gx * M + gy) * M + gz;
   };
   if (kMorton) {
     const int64_t base =
@@ -222,7 +226,7 @@ __global__ void __launch_bounds__(256) k_cic_gather(const int32_t* __restrict__ 
     for (int o = 0; o < 8; ++o) {
       const int ox = (o >> 2) & 1, oy = (o >> 1) & 1, oz = o & 1;
       const int32_t f = first[q0 - ox * 81 - oy * 9 - oz];
-      acc += f >= 0 ? W[8 * (int64_t)f + o] : (R)0;
+      acc += f >= 0 ? W[8 * f + o] : (R)0;  // 8 f + o < 8 cap <= 2^30
     }
     delta[((int64_t)(bx + a) * M + (by + b)) * M + (bz + c)] = acc * inv_nbar - (R)1;
   }
