@@ -366,17 +366,7 @@ __global__ void __launch_bounds__(256) k_pm_interp_tile(const int32_t* __restric
 
 // the deposit reads the depth-m cell table the tree build wrote for the same keys
 template <class R>
-void pm_smem_attributes() {
-  static bool done = false;  // once per process and type (the attribute is per function)
-  if (done) return;
-  cudaFuncSetAttribute(k_cic_gather<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gather_smem<R>());
-  cudaFuncSetAttribute(k_cic_gather<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gather_smem<R>());
-  done = true;
-}
-
-template <class R>
 void pm_deposit(dzs_ctx* c) {
-  pm_smem_attributes<R>();
   Buffers& B = c->B;
   const int M = c->M;
   const int64_t m3 = (int64_t)M * M * M;
