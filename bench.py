@@ -274,6 +274,12 @@ def cpu_baseline(steps_cap=96):
                       "spacing and DZS parameters, FP64 oracle, %.1f s" % (n, dt)}
 
 
+def workload_name(warmup, steps):
+    """the bench workload, as both arms name it in `config`"""
+    return ("single lightcone mock: N=128^3, L=256 Mpc/h, mesh 256^3, FP32 forces (u32 lattice positions), "
+            "DZS merge level 3, 96 KDK steps z=49->0, steps %d..%d timed" % (warmup, warmup + steps - 1))
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -300,11 +306,13 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": "FP64 CPU oracle, 32^3 particles in 64 Mpc/h (mesh 64^3), "
-                                                       "same spacing and DZS parameters as the 128^3 mock",
-                                            "parallelism": "host cores"},
+            "data": "synthetic",
+            "config": {"workload": workload_name(args.warmup, args.steps), "global_batch": 128 ** 3,
+                       "parallelism": "host cores (%d threads)" % cores},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": "%d oracle steps of the 32^3 sub-box" % args.steps},
+                             "sample": "each step: one FP64 oracle step of a 32^3-particle, 64 Mpc/h sub-box (mesh "
+                                       "64^3) with the mock's particle and mesh spacing and DZS parameters; "
+                                       "particle-steps/s of the sample"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -472,9 +480,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "single lightcone mock: N=128^3, L=256 Mpc/h, mesh 256^3, FP32 forces (u32 lattice "
-                               "positions), DZS merge level 3, 96 KDK steps z=49->0, steps %d..%d timed"
-                               % (args.warmup, args.warmup + args.steps - 1),
+        "config": {"workload": workload_name(args.warmup, args.steps),
                    "global_batch": n0 * world, "parallelism": "replicas x%d" % world,
                    "l2": "inputs larger than L2 (state + 256^3 mesh > 129 MB)", "restarts_in_timed_region": relaunch,
                    "n_active_end": int(n_final)},
