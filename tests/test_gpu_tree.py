@@ -7,8 +7,10 @@ The node count and the group count of the CUDA tree (built without a pass per
 depth) equal those of a plain recursive top-down split of the sorted keys
 written here, and the group count equals the oracle's; inputs: clustered sets
 of several sizes, B and G, sets of at most B and at most G particles, runs of
-coincident particles, and a lattice.  The accelerations through the same tree
-match the oracle (FP64) on each input."""
+coincident particles, and a lattice.  The number of (particle, list entry)
+pairs the walk evaluates equals the oracle's interaction count exactly (the
+same interaction sets, whatever node the walk starts from), and the
+accelerations through the same tree match the oracle (FP64) on each input."""
 import numpy as np
 import pytest
 
@@ -107,6 +109,9 @@ def test_tree_counts_match_definition(dzs, name, u, extra):
     assert cnt[3] == 0
     assert cnt[0] == groups, (name, cnt[0], groups)
     assert cnt[1] == nodes, (name, cnt[1], nodes)
+    # the interaction set: every particle's list length summed, exactly the
+    # oracle's (monopoles and leaf particles per group, times its particles)
+    assert cnt[2] == O.interaction_count(P, us, state["k"]), (name, cnt[2])
     # a lattice's exact force is 0: scale by the pair force at the mean spacing,
     # G m0 / (L / N1)^2, G m0 = 1.5 Omega_m L^3 / (4 pi N1^3)
     spacing = kw["box"] / kw["n1d"]

@@ -81,6 +81,16 @@ def test_sigma8_normalisation_scipy():
 
     s2 = quad(integrand, math.log(1e-5), math.log(50.0), limit=500, epsabs=0, epsrel=1e-10)[0]
     assert math.sqrt(s2) == pytest.approx(0.8, rel=1e-6)
+    # the oracle's own top-hat sigma(r): sigma8 at 8 Mpc/h, and the same
+    # integral at another radius
+    assert O.sigma_r(P, 8.0) == pytest.approx(0.8, rel=1e-6)
+
+    def integrand4(lnk):
+        k = math.exp(lnk)
+        return k ** 3 * amp * O.lib().dzso_power_shape(O.byref(P), k) * w(4 * k) ** 2 / (2 * math.pi ** 2)
+
+    s4 = quad(integrand4, math.log(1e-5), math.log(100.0), limit=500, epsabs=0, epsrel=1e-10)[0]
+    assert O.sigma_r(P, 4.0) == pytest.approx(math.sqrt(s4), rel=1e-6)
 
 
 def test_bbks_shape():
