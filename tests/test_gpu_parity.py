@@ -156,6 +156,8 @@ def test_accel_c1_fp64_all_particles(dzs):
         cnt = ctx.counters()
     assert gerr(got, want).max() <= 1e-9
     assert cnt[0] > 0 and cnt[2] > 0 and cnt[3] == 0
+    # the same interaction sets: evaluated (particle, entry) pairs, exactly
+    assert cnt[2] == O.interaction_count(P, st["u"], st["k"])
 
 
 def test_pm_mesh_delta(dzs):
