@@ -10,8 +10,9 @@ closing kick).  W warm-up steps start from the ICs; the K timed steps continue
 the run (when the run reaches a = 1 it restarts from fresh ICs outside the
 timed region).  value = N_init x K / device time ("effective" particle-steps/s).
 
---impl reference times the FP64 CPU oracle (the reference arm of this build)
-on the same metric, on a 32^3 sub-box with the same particle and mesh spacing.
+--impl reference times the FP64 CPU oracle (there is no other reference
+implementation) on the same metric and workload name, each step on a 32^3
+sub-box with the same particle and mesh spacing.
 """
 import argparse
 import json
@@ -34,12 +35,11 @@ UNIT = "particle-steps/s"
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # FP32 arithmetic of one pair evaluation of the walk (FMA = 2; rsqrt, exp2 = 1):
 # r^2 6, rsqrt 1, r 1, r^-3 2, t 2, split polynomial 22, exp 3 (r^2 scale, exp2,
-# times Q), force 2, accumulate 6 ("walk roofline")
+# times Q), force 2, accumulate 6
 FLOP_PER_PAIR = 45
 
 # algorithmic HBM bytes per step of the streaming stages, FP32 state
-# (u 12 B, p 12 B, g 12 B, k 4 B, id 4 B, flags 1 B per particle; mesh M^3);
-# derivation in DESIGN.md ("per-stage bytes")
+# (u 12 B, p 12 B, g 12 B, k 4 B, id 4 B, flags 1 B per particle; mesh M^3)
 STAGE_BYTES = {
     "kick_drift": lambda n, m3: 90 * n,
     "sort": lambda n, m3: 326 * n,

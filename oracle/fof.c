@@ -5,7 +5,7 @@
  * Paper Sec. 3.1.1: the lightcone halo mass function is built from the FoF
  * halo catalogues of frequent outputs (the FoF finder of the simulation code),
  * keeping the haloes entirely inside the lightcone at the time of each output.
- * Reading (the paper gives no linking length; DESIGN.md): two particles are
+ * Reading (the paper gives no linking length): two particles are
  * friends when their minimum-image lattice distance satisfies
  *     d^2 <= T,   T = floor((link * 2^32 / n1d)^2)   (FP64, then integer),
  * i.e. d <= link * lambda with lambda = L / n1d the initial mean spacing; a

@@ -9,7 +9,7 @@
  * opening rule with d replaced by the node distance of Eq. 3,
  *   D_n = max(d_{n-obs} - R_lc - b, 0),   merge iff l_n / D_n < theta_dzs,
  * with node sizes limited to l_n <= l_max (Sec. 2.2).  Readings where the
- * paper is silent (see DESIGN.md):
+ * paper is silent:
  *   - cells are octree cells of side L / 2^j down to depth 21; a cell with a
  *     single particle is left alone; l_max = 2^(merge_level-1) lambda;
  *   - integer test: merge iff d_COM^2 > T^2, T = R_lat + b_lat + ceil(l_lat /

@@ -16,8 +16,9 @@
  *     Eq. 3 and the geometric criterion l_n / D_n < theta (Sec. 2.2.1);
  *   - the lightcone shell crossing at R_lc(a) (Sec. 1 footnote, Sec. 3.1.3);
  *   - global KDK steps (Sec. 2.1: DZS runs only on global steps).
- * Where the paper is silent the oracle takes the readings listed in the design doc
- * (lattice positions, ICs, cubic-spline softening, group walk, ...).
+ * Where the paper is silent the oracle takes its own stated readings (lattice
+ * positions, ICs, cubic-spline softening, group walk, ...), each written out in
+ * the file that implements it.
  *
  * Parity status: every function below is pinned by tests/test_oracle_*.py
  * against closed forms, brute force or invariants, except

@@ -2,7 +2,7 @@
 a_lm (Sec. 3.1.2, the angular power spectrum of the lightcone sky map) of the
 oracle's Nside = 256 sky map of 2,000,000 seeded records, for degrees above
 the range of scipy's sph_harm_y (the oracle then evaluates Y_lm with mpmath,
-which the GPU machine does not have).  Calls only oracle/.  Run from the repo
+which GPU test hosts may lack).  Calls only oracle/.  Run from the repo
 root: python tests/golden/make_alm_golden.py"""
 import hashlib
 import json
