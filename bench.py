@@ -31,32 +31,47 @@ sys.path.insert(0, ROOT)
 
 METRIC = "particle-steps/s DZS FP32 vs plain FP64 at stated force error; mocks/h, p99 lat"
 UNIT = "particle-steps/s"
-# nominal FP32 pipe: 152 SMs x 128 lanes x 2 flop (FMA) x 2.07 GHz max SM clock
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-# FP32 arithmetic of one pair evaluation of the walk (FMA = 2; rsqrt, exp2 = 1):
-# r^2 6, rsqrt 1, r 1, r^-3 2, t 2, split polynomial 22, exp 3 (r^2 scale, exp2,
-# times Q), force 2, accumulate 6
-FLOP_PER_PAIR = 45
+# FP32 arithmetic of one in-range pair evaluation of the walk (Sec. 2.1 pair
+# force), counted from the code on the FMA pipe (FFMA = 2, FMUL/FADD = 1):
+# r^2 6 (FMUL + 2 FFMA + bias add), r = r^2 / sqrt 1, r^-3 2, polynomial
+# variable 2, split polynomial 22 (11 FFMA), exp2 argument 1, exp times Q 1,
+# force 2, accumulate 6; plus 2 SFU operations (rsqrt, exp2).  A listed pair
+# beyond r_cut costs only the r^2 test (6 flop) and is not algorithmic work.
+FMA_FLOP_PER_PAIR = 43
+SFU_OPS_PER_PAIR = 2
 
-# algorithmic HBM bytes per step of the streaming stages, FP32 state
-# (u 12 B, p 12 B, g 12 B, k 4 B, id 4 B, flags 1 B per particle; mesh M^3)
+# algorithmic HBM bytes per step of the streaming stages (FP32 state: u 12 B,
+# p 12 B, g 12 B, k 4 B, flags 1 B per particle; mesh M^3 cells of 4 B):
+# kick/drift/crossing reads u, p, g, k, flags and writes u, p, flags, key
+# (74 B); the sort moves the state once (2 x 45 B); the tree ~10 B; the CIC
+# deposit reads u, k (16 B) and writes the mesh (4 B per cell); the FFT
+# Poisson solve at best reads and writes the mesh once each way (4 x 4 B per
+# cell); the gradient + interpolation reads phi (4 B per cell) and u, writes g
+# (24 B); the merge ~30 B on steps where it runs
 STAGE_BYTES = {
+    "kick_drift": lambda n, m3: 74 * n,
+    "sort": lambda n, m3: 90 * n,
+    "merge": lambda n, m3: 30 * n,
+    "tree": lambda n, m3: 10 * n,
+    "pm": lambda n, m3: 16 * n + 4.0 * m3 + 4.0 * m3 + 24 * n,
+    "fft": lambda n, m3: 16.0 * m3,
+}
+# the implementation's own bytes per step (what its kernels read and write,
+# counted from the code), reported beside the algorithmic bytes
+IMPL_BYTES = {
     "kick_drift": lambda n, m3: 90 * n,
     "sort": lambda n, m3: 326 * n,
     "merge": lambda n, m3: 194 * n,
     "tree": lambda n, m3: 95 * n,
-    # CIC deposit (cell bounds 8 B, delta 4 B per cell; u, k 16 B per particle)
-    # and gradient + interpolation (phi 4 B per cell; u 12 B in, g 12 B out)
     "pm": lambda n, m3: 16.0 * m3 + 40 * n,
-    # five passes over the mesh: Z r2c, Y, X with the Green multiply, Y^-1, Z c2r
     "fft": lambda n, m3: 40.3 * m3,
 }
 
-# DRAM bytes (read + write) of one k_walk launch from an ncu capture (step 41 of
-# the bench run, z ~ 4) and the walk source it was taken on: reported as
-# roofline traffic only while the source is unchanged
-WALK_TRAFFIC_BYTES = 172.605e6 + 35.825e6
-WALK_TRAFFIC_SRC = "86812881f7ef2e16"
+# DRAM bytes (read + write) of one k_walk launch from an ncu capture and the
+# walk source it was taken on: reported as roofline traffic only while the
+# source is unchanged
+WALK_TRAFFIC_BYTES = None
+WALK_TRAFFIC_SRC = None
 
 # serving sample (Poisson stream of mock requests, sizes 32^3 .. 256^3)
 SERVE_RATE = 4.0
@@ -354,6 +369,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the plain-FP64 and no-DZS runs")
     ap.add_argument("--serve-requests", type=int, default=24, help="serving sample size (0: skip)")
+    ap.add_argument("--profile-window", default=None, metavar="SKIP,STEPS",
+                    help="run the bench mock for SKIP + STEPS steps and print the kernel launches before and in "
+                         "the last STEPS (for ncu -s / -c); no timing")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -376,6 +394,10 @@ def main():
     if world > 1:
         dist.barrier()
     dzs.load()
+    if args.profile_window:
+        a, b = (int(x) for x in args.profile_window.split(","))
+        profile_window(dzs, a, b)
+        return
     stream = torch.cuda.Stream()
     P = workload_params(dzs, dzs.FP32)
     P.device = local
@@ -433,49 +455,66 @@ def main():
         prof = ctx.profile()
         cnt = ctx.counters()
         launches = int(cnt[4]) - l0
-        pairs = int(cnt[2])
+        wc = ctx.walk_counters()
+        pairs, pairs_in = int(wc[0]), int(wc[1])
         n_final, _ = ctx.count()
     t_local = ms / 1e3
     units_total, t_max = R.aggregate(n0 * args.steps, t_local,
                                      device=torch.device("cuda", local) if world > 1 else None)
     value = R.throughput(units_total, t_max)
 
-    # e2e through the public API with host buffers (rank 0 measures, others replicate)
+    # e2e through the public API with host buffers, over the same steps as
+    # `value` (rank 0 measures, others replicate)
     e2e = None
     if not args.no_e2e:
-        e2e = measure_e2e(dzs, P, stream, min(args.steps, nst))
+        e2e = measure_e2e(dzs, P, stream, args.warmup, args.steps)
 
     if rank != 0:
         return
-    # HBM rooflines of the streaming stages (algorithmic bytes / stage time)
+    # HBM rooflines of the streaming stages: algorithmic bytes (the per-stage
+    # bytes per particle-step above) / stage time, beside the implementation's
+    # own bytes
     counts = active_counts(dzs, P, stream, args.warmup, args.steps)
     m3 = P.mesh ** 3
     pk = peaks()
     hbm = float(pk.get("hbm_gbs", 6800.0))  # measured copy bandwidth, else the 6.8 TB/s fallback
+    hbm_src = "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in pk else "fallback 6.8 TB/s"
     stage_roof = {}
     for name, fn in STAGE_BYTES.items():
-        ms_s = prof[name][0]
+        ms_s, calls = prof[name]
         if ms_s <= 0:
             continue
-        gb = sum(fn(n, m3) for n in counts) / 1e9
+        if name == "merge":  # merge steps only
+            gb = calls * 30 * float(np.mean(counts)) / 1e9
+        else:
+            gb = sum(fn(n, m3) for n in counts) / 1e9
+        impl = sum(IMPL_BYTES[name](n, m3) for n in counts) / 1e9
         stage_roof[name] = {"bound": "hbm", "algorithmic_GB": gb, "achieved_GBs": gb / (ms_s / 1e3),
-                            "frac": gb / (ms_s / 1e3) / hbm}
-    # roofline of the dominant stage
+                            "frac": gb / (ms_s / 1e3) / hbm, "impl_GB": impl,
+                            "impl_GBs": impl / (ms_s / 1e3), "calls": calls, "peak_GBs": hbm, "peak_source": hbm_src}
+    # roofline of the dominant kernel, the tree walk: FP32 FMA-pipe flops of the
+    # in-range pair evaluations against the measured FMA peak (SFU ops beside)
     dom = max(prof, key=lambda k: prof[k][0])
     walk_ms, walk_calls = prof["walk"]
     walk_avg_s = walk_ms / 1e3 / max(1, walk_calls)
-    achieved_tf = pairs / max(1, walk_calls) * FLOP_PER_PAIR / walk_avg_s / 1e12
+    fma_peak, sfu_peak = dzs.dzs_measure_fp32_peaks(local, 5)
+    in_per_launch = pairs_in / max(1, walk_calls)
+    achieved_tf = in_per_launch * FMA_FLOP_PER_PAIR / walk_avg_s / 1e12
+    sfu_gops = in_per_launch * SFU_OPS_PER_PAIR / walk_avg_s / 1e9
     import hashlib
     wsrc = hashlib.sha256(open(os.path.join(ROOT, "paper_2005_05328_gb300", "csrc", "walk.cu"), "rb").read())
     traffic = WALK_TRAFFIC_BYTES if wsrc.hexdigest()[:16] == WALK_TRAFFIC_SRC else None
     roof = {"bound": "alu", "kernel": "k_walk<float> (tree walk + closing kick)", "achieved": achieved_tf,
-            "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved_tf / FP32_PEAK_TFLOPS, "traffic": traffic,
-            "traffic_note": "bytes of the step-41 launch (ncu, one capture); the timed launches average "
-                            "over z = 49 -> 0",
-            "peak_source": "nominal FP32 FMA rate 152 SM x 128 lanes x 2 x 2.07 GHz (no measured FP32 peak in "
-                           "MEASURED_PEAKS.json)",
-            "pairs_per_launch": pairs / max(1, walk_calls), "flop_per_pair": FLOP_PER_PAIR,
-            "avg_launch_ms": walk_avg_s * 1e3, "dominant_stage": dom}
+            "peak": fma_peak, "unit": "TFLOP/s", "frac": achieved_tf / fma_peak, "traffic": traffic,
+            "peak_source": "measured: FP32 FMA-chain micro-benchmark on this GPU (dzs_measure_fp32_peaks, "
+                           "best of 5, timed alone)",
+            "flop_per_in_range_pair": FMA_FLOP_PER_PAIR, "in_range_pairs_per_launch": in_per_launch,
+            "listed_pairs_per_launch": pairs / max(1, walk_calls),
+            "in_range_fraction": pairs_in / max(1, pairs),
+            "sfu": {"achieved_Gops": sfu_gops, "peak_Gops": sfu_peak, "frac": sfu_gops / sfu_peak,
+                    "ops_per_in_range_pair": SFU_OPS_PER_PAIR},
+            "avg_launch_ms": walk_avg_s * 1e3, "launches": walk_calls, "dominant_stage": dom,
+            "sm_count": torch.cuda.get_device_properties(local).multi_processor_count}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -509,7 +548,9 @@ def main():
         comp["cufft_256cubed_r2c_green_c2r"] = {"ms": cu, "ours_ms": fft_ms, "ours_over_cufft_time": fft_ms / cu,
                                                 "note": "torch.fft (cuFFT) rfftn * G + irfftn, FP32, same mesh"}
         line["comparisons"] = comp
-    line["config"]["mocks_per_h_single_stream"] = 3600.0 / (P.nsteps * ms / args.steps / 1e3)
+    if world == 1 and not args.no_compare:
+        line["full_run"] = full_run(dzs, P, stream)
+        line["config"]["mocks_per_h_single_stream"] = line["full_run"]["mocks_per_h"]
     line["config"]["actual_particle_steps_per_s"] = sum(counts) / (ms / 1e3)  # sum of N_active per step
     if world == 1 and args.serve_requests > 0:
         line["serving"] = serving_sample(dzs, args.serve_requests, 4)
@@ -517,34 +558,46 @@ def main():
         line["batched"] = batched_sample(dzs)
         line["large_instance"] = c3_sample(dzs, stream)
     if world == 1 and not args.no_cpu_baseline:
+        # the cpu_baseline leg: the oracle timed on the host cores, and the
+        # oracle's FP64 forces on sampled particles of the mock's own states
+        # (the stated force error of the measured FP32 path)
         try:
             line["cpu_baseline"] = cpu_baseline()
         except Exception as ex:  # the oracle needs gcc; report why it is missing
             line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                                     "sample": "unavailable: %s" % ex}
+        try:
+            line["force_error"] = force_error(dzs, P, stream)
+        except Exception as ex:
+            line["force_error"] = {"unavailable": str(ex)}
     print(json.dumps(line), flush=True)
 
 
-def measure_e2e(dzs, P, stream, k):
-    """Same metric through the C ABI with host buffers: the IC state is copied
-    in from pinned host memory, then every step runs and its lightcone records
-    and diagnostics are copied back to the host."""
+def measure_e2e(dzs, P, stream, warmup, steps):
+    """The same metric through the C ABI with host buffers, over the steps
+    `value` times: the state after the warm-up steps is read back (untimed);
+    the timed region copies it in from pinned host memory, runs the steps and
+    copies every step's lightcone records and diagnostics back to the host."""
     import torch
     ctx = dzs.Context(P, stream=stream.cuda_stream)
+    k = min(steps, P.nsteps - warmup) if warmup < P.nsteps else 0
     with torch.cuda.stream(stream):
         ctx.ics()
+        ctx.step(warmup)
         st = ctx.state()
+        ctx.drain(cap=st["u"].shape[1])
         n = st["u"].shape[1]
         pinned = {}
         for key, arr in st.items():
             t = torch.empty(arr.shape, dtype={np.uint32: torch.int32, np.float64: torch.float64,
-                                              np.uint8: torch.uint8}[arr.dtype.type], pin_memory=True)
+                                              np.float32: torch.float32, np.uint8: torch.uint8}[arr.dtype.type],
+                            pin_memory=True)
             t.numpy().view(arr.dtype)[...] = arr
             pinned[key] = t.numpy().view(arr.dtype)
         h2d = sum(a.nbytes for a in pinned.values())
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ctx.set_state(pinned, 0)
+        ctx.set_state(pinned, warmup)
         d2h = 0
         for _ in range(k):
             ctx.step(1)
@@ -554,8 +607,88 @@ def measure_e2e(dzs, P, stream, k):
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
     ctx.close()
-    return {"value": P.n1d ** 3 * k / wall, "unit": UNIT, "h2d_bytes_per_step": h2d / k,
-            "d2h_bytes_per_step": d2h / k, "steps": k}
+    return {"value": P.n1d ** 3 * k / wall, "unit": UNIT, "h2d_bytes_per_step": h2d / max(1, k),
+            "d2h_bytes_per_step": d2h / max(1, k), "steps": k, "first_step": warmup,
+            "note": "state after the warm-up steps copied in from pinned host memory once; every step's records "
+                    "and diagnostics copied back"}
+
+
+def full_run(dzs, P, stream):
+    """One whole mock (ICs + all steps + the lightcone drained after every
+    step), host wall clock: the single-stream mocks/h"""
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx = dzs.Context(P, stream=stream.cuda_stream)
+    nrec = 0
+    with torch.cuda.stream(stream):
+        ctx.ics()
+        for _ in range(P.nsteps):
+            ctx.step(1)
+            nrec += len(ctx.drain(cap=P.n1d ** 3))
+        n_end, _ = ctx.count()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    ctx.close()
+    return {"wall_s": wall, "mocks_per_h": 3600.0 / wall, "steps": P.nsteps, "records": nrec,
+            "n_active_end": int(n_end), "effective_particle_steps_per_s": P.n1d ** 3 * P.nsteps / wall}
+
+
+FORCE_STEPS = ((1, "z~49"), (62, "z~3"), (79, "z~1"), (96, "z=0"))
+
+
+def force_error(dzs, P, stream, nsample=3000):
+    """FP32 force error of the measured path against the FP64 oracle on the
+    mock's own evolved states (after steps 1, 62, 79, 96: z ~ 49, 3, 1, 0):
+    |g_gpu - g_oracle| / (|g_oracle| + 1e-3 g_rms) on `nsample` random
+    particles of each state (the oracle evaluates only their walk groups and
+    the PM mesh); untimed, rank 0."""
+    import oracle as O
+    os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
+    Po = O.params(n1d=P.n1d, mesh=P.mesh, box=P.box, merge_level=P.merge_level, seed=P.seed, sigma8=P.sigma8)
+    ctx = dzs.Context(P, stream=stream.cuda_stream)
+    out = {}
+    rng = np.random.default_rng(12345)
+    t0 = time.perf_counter()
+    import torch
+    with torch.cuda.stream(stream):
+        ctx.ics()
+        done = 0
+        for step, name in FORCE_STEPS:
+            ctx.step(step - done)
+            done = step
+            st = ctx.state()
+            n = st["u"].shape[1]
+            idx = np.sort(rng.choice(n, size=min(nsample, n), replace=False))
+            want = O.accel(Po, st["u"], st["k"], sample=idx)[:, idx]
+            got = st["g"][:, idx]
+            ref = np.linalg.norm(want, axis=0)
+            rel = np.linalg.norm(got - want, axis=0) / (ref + 1e-3 * np.sqrt((ref ** 2).mean()))
+            out[name] = {"step": step, "n_active": n, "sampled": len(idx), "p50": float(np.percentile(rel, 50)),
+                         "p99": float(np.percentile(rel, 99)), "p99.9": float(np.percentile(rel, 99.9)),
+                         "max": float(rel.max())}
+    ctx.close()
+    out["bound"] = "99.9th percentile <= 1e-4 (FP32 accelerations vs the FP64 oracle on the same state)"
+    out["metric"] = "|g_gpu - g_oracle| / (|g_oracle| + 1e-3 g_rms) per sampled particle"
+    out["oracle_s"] = time.perf_counter() - t0
+    return out
+
+
+def profile_window(dzs, skip, steps):
+    """Run the bench mock from the ICs through `skip` steps, then `steps`
+    more; print '<library kernel launches before the window> <launches in
+    it>' so that an ncu command can select exactly the window's launches
+    (-s / -c)."""
+    import torch
+    P = workload_params(dzs, dzs.FP32)
+    with dzs.Context(P) as ctx:
+        ctx.ics()
+        ctx.step(skip)
+        n0 = int(ctx.counters()[4])
+        ctx.step(steps)
+        n1 = int(ctx.counters()[4])
+    torch.cuda.synchronize()
+    print(n0, n1 - n0)
 
 
 if __name__ == "__main__":

@@ -376,6 +376,24 @@ DZS_API dzs_status dzs_get_mesh(dzs_ctx* c, int32_t which, double* out);
  * [7] tree-walk node tests and [8] traversal rounds summed like [2]. */
 DZS_API dzs_status dzs_get_counters(dzs_ctx* c, uint64_t out[9]);
 
+/* Tree-walk work counters (Sec. 2.1 short-range force), summed like
+ * dzs_get_counters' [2]: [0] listed pairs (interaction-list entries x group
+ * particles, the same count as dzs_get_counters [2]), [1] pairs evaluated in
+ * range (0 < r < r_cut: the pairs that carry force), [2] node tests, [3]
+ * traversal rounds.  Synchronises the context stream. */
+DZS_API dzs_status dzs_get_walk_counters(dzs_ctx* c, uint64_t out[4]);
+
+/* Interaction lists of the last tree walk, per walk group (Eq. 1 applied per
+ * group: a node with <= walk_group particles whose parent holds more, or a
+ * leaf): first particle (index in the current Morton order), particle count
+ * and interaction-list length (accepted monopoles + particles of opened
+ * leaves).  *ngroups receives the number of groups; any of first, count,
+ * list_len may be NULL (all NULL: only the count); cap below the number of
+ * groups is DZS_EINVAL.  Group order is the library's (by tree node).
+ * Synchronises the context stream. */
+DZS_API dzs_status dzs_walk_lists(dzs_ctx* c, int64_t* first, int64_t* count, int64_t* list_len, size_t cap,
+                                  size_t* ngroups);
+
 /* profile categories of dzs_get_profile */
 enum {
   DZS_PROF_KICK_DRIFT = 0, /* opening kick, drift, crossing, record compaction */
@@ -416,8 +434,12 @@ DZS_API dzs_status dzs_get_profile(dzs_ctx* c, double ms[DZS_PROF_N], uint64_t c
  *   stream  cudaStream_t the work is enqueued on (NULL = legacy stream).
  * Allocates nothing: no cudaMalloc, cudaFree or allocating library call.
  * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  Every call shares the one array and leaves its contents behind
+ * device, with that device current) and keeps it for the life of the process;
+ * make that first call before any stream capture.  A cudaDeviceReset destroys
+ * the array with the context that held it: do not call this entry point on
+ * that device after a reset.  A CUDA error already pending on the calling
+ * thread makes the call return DZS_ECUDA before it launches anything (the
+ * error is left pending for its owner).  Every call shares the one array and leaves its contents behind
  * (each call writes every scratch word it reads before reading it), so calls
  * whose work overlaps on the GPU -- on two streams, or from two threads --
  * race and must be serialised by the caller.  Returns DZS_EINVAL for
@@ -425,6 +447,17 @@ DZS_API dzs_status dzs_get_profile(dzs_ctx* c, double ms[DZS_PROF_N], uint64_t c
  * no device is current, DZS_ECUDA when a CUDA call fails; asynchronous. */
 DZS_API dzs_status dzs_morton_sort_noalloc(const uint32_t* d_u, size_t n, uint32_t* d_perm, uint64_t* d_keys,
                                            void* cuda_stream);
+
+/* Measured FP32 arithmetic peaks of a device (the roofline denominators of the
+ * tree walk, whose pair arithmetic of Sec. 2.1 runs on the FP32 FMA pipe and
+ * the special-function unit): FMA-chain and reciprocal-square-root-chain
+ * micro-benchmarks over every SM, timed with CUDA events, best of `reps`
+ * launches after one warm-up.  *fma_tflops: FP32 TFLOP/s (an FFMA counts 2
+ * flop); *sfu_gops: SFU operations per second / 1e9.  Either output may be
+ * NULL (its kernel is then skipped), not both.  Allocates a few bytes of
+ * device memory for the duration of the call and restores the current device.
+ * Synchronous; DZS_EINVAL for reps < 1, DZS_EDEVICE / DZS_ECUDA on failure. */
+DZS_API dzs_status dzs_measure_fp32_peaks(int32_t device, int32_t reps, double* fma_tflops, double* sfu_gops);
 
 /* Message of the last failure on this context (valid until the next call).
  * c may be NULL (then: the last dzs_create failure of this thread). */

@@ -33,7 +33,7 @@ PK_SHOT = 1
 EXPORTED = ["dzs_params_default", "dzs_footprint_bytes", "dzs_create", "dzs_ics", "dzs_step",
             "dzs_run_stages", "dzs_lightcone_drain", "dzs_destroy", "dzs_get_count", "dzs_get_state",
             "dzs_set_state", "dzs_accel", "dzs_merge_only", "dzs_diagnostics", "dzs_get_tables",
-            "dzs_get_mesh", "dzs_get_counters", "dzs_set_profiling", "dzs_get_profile",
+            "dzs_get_mesh", "dzs_get_counters", "dzs_get_walk_counters", "dzs_walk_lists", "dzs_measure_fp32_peaks", "dzs_set_profiling", "dzs_get_profile",
             "dzs_morton_sort_noalloc", "dzs_checkpoint_bytes", "dzs_checkpoint", "dzs_restore",
             "dzs_step_until", "dzs_observe_enable", "dzs_observe_add_records", "dzs_skymap_get",
             "dzs_lcdensity_get", "dzs_skymap_alm", "dzs_power_spectrum", "dzs_serve", "dzs_fof", "dzs_last_error"]
@@ -119,7 +119,9 @@ def load(path: str = LIB_PATH):
         "dzs_set_state": [vp, vp, vp, vp, vp, vp, vp, sz, i32],
         "dzs_accel": [vp, i32, vp], "dzs_merge_only": [vp, u64], "dzs_diagnostics": [vp, vp],
         "dzs_get_tables": [vp, vp, vp, vp, vp, vp, vp], "dzs_get_mesh": [vp, i32, vp],
-        "dzs_get_counters": [vp, vp], "dzs_set_profiling": [vp, i32], "dzs_get_profile": [vp, vp, vp],
+        "dzs_get_counters": [vp, vp], "dzs_get_walk_counters": [vp, vp],
+        "dzs_walk_lists": [vp, vp, vp, vp, sz, C.POINTER(sz)],
+        "dzs_measure_fp32_peaks": [i32, i32, C.POINTER(C.c_double), C.POINTER(C.c_double)], "dzs_set_profiling": [vp, i32], "dzs_get_profile": [vp, vp, vp],
         "dzs_checkpoint_bytes": [vp, C.POINTER(sz)], "dzs_checkpoint": [vp, vp, sz, C.POINTER(sz)],
         "dzs_restore": [vp, vp, sz],
         "dzs_step_until": [vp, i32, C.POINTER(Halt), C.POINTER(i32), C.POINTER(i32), C.POINTER(C.c_double)],
@@ -276,6 +278,32 @@ def dzs_get_counters(h):
     return out
 
 
+def dzs_get_walk_counters(h):
+    """[listed pairs, in-range pairs, node tests, traversal rounds]"""
+    out = np.zeros(4, np.uint64)
+    _check(load().dzs_get_walk_counters(h, _ptr(out)), h)
+    return out
+
+
+def dzs_measure_fp32_peaks(device=0, reps=5):
+    """(FP32 FMA TFLOP/s, SFU Gop/s) measured on `device`"""
+    f, s = C.c_double(0), C.c_double(0)
+    st = load().dzs_measure_fp32_peaks(device, reps, C.byref(f), C.byref(s))
+    if st != DZS_OK:
+        raise RuntimeError("dzs_measure_fp32_peaks failed with status %d" % st)
+    return f.value, s.value
+
+
+def dzs_walk_lists(h):
+    """per walk group of the last walk: (first particle, count, list length)"""
+    ng = C.c_size_t(0)
+    _check(load().dzs_walk_lists(h, None, None, None, 0, C.byref(ng)), h)
+    n = ng.value
+    first = np.zeros(n, np.int64); cnt = np.zeros(n, np.int64); ln = np.zeros(n, np.int64)
+    _check(load().dzs_walk_lists(h, _ptr(first), _ptr(cnt), _ptr(ln), n, C.byref(ng)), h)
+    return first, cnt, ln
+
+
 def dzs_morton_sort_noalloc(d_u: int, n: int, d_perm: int, d_keys: int = 0, stream: int = 0) -> int:
     """Allocation-free Morton sort on caller-owned device buffers (raw device
     addresses, e.g. torch tensor data_ptr()); returns the dzs_status code.
@@ -420,6 +448,8 @@ class Context:
     def tables(self): return dzs_get_tables(self.h, self.params.nsteps)
     def mesh(self, which): return dzs_get_mesh(self.h, which, self.params.mesh)
     def counters(self): return dzs_get_counters(self.h)
+    def walk_counters(self): return dzs_get_walk_counters(self.h)
+    def walk_lists(self): return dzs_walk_lists(self.h)
     def set_profiling(self, on=True): dzs_set_profiling(self.h, on)
     def profile(self): return dzs_get_profile(self.h)
     def checkpoint(self): return dzs_checkpoint(self.h)

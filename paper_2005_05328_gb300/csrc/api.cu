@@ -86,7 +86,7 @@ struct Plan {
   int64_t cap, node_cap, m3, nspec, nb, nchunks, ring;
   size_t rsz;
   size_t o_u, o_u2, o_p, o_p2, o_g, o_gsave, o_k, o_k2, o_id, o_id2, o_fl, o_fl2, o_key, o_key2, o_idx, o_idx2, o_hist,
-      o_blocksum, o_iscan, o_prefix, o_mend, o_nodes, o_lvl, o_nsum, o_parent, o_arrive, o_cicw, o_groups, o_ghead, o_wpm, o_wph, o_wnh,
+      o_blocksum, o_iscan, o_prefix, o_mend, o_nodes, o_lvl, o_nsum, o_parent, o_arrive, o_cicw, o_groups, o_ghead, o_wpm, o_wph, o_wnh, o_wlen,
       o_rho, o_spec, o_phi,
       o_cstart, o_tw, o_green, o_ring, o_n, o_err, o_counters, o_diag, o_convert;
   size_t total;
@@ -132,6 +132,7 @@ struct Plan {
     o_wpm = L.take((rsz == 8 ? 24 : 16) * cap);  // packed walk entries: lattice position, G m
     o_wph = L.take(rsz * cap);
     o_wnh = L.take(rsz * node_cap);
+    o_wlen = L.take(4 * cap);
     o_rho = L.take(rsz * m3);
     o_spec = L.take(2 * rsz * nspec);
     o_phi = L.take(rsz * m3);
@@ -141,7 +142,7 @@ struct Plan {
     o_ring = L.take(sizeof(dzs_lc_record) * ring);
     o_n = L.take(16);
     o_err = L.take(16);
-    o_counters = L.take(8 * 16);
+    o_counters = L.take(8 * 32);
     o_diag = L.take(8 * (8 + 3 * 304));
     o_convert = L.take(8 * 3 * cap);
     total = L.total;
@@ -397,6 +398,7 @@ dzs_status dzs_create(const dzs_params* p, void* cuda_stream, dzs_ctx** out) {
   B.wpm = a + pl.o_wpm;
   B.wph = a + pl.o_wph;
   B.wnh = a + pl.o_wnh;
+  B.wlen = (int32_t*)(a + pl.o_wlen);
   B.rho = a + pl.o_rho;
   B.spec = a + pl.o_spec;
   B.phi = a + pl.o_phi;
@@ -410,7 +412,7 @@ dzs_status dzs_create(const dzs_params* p, void* cuda_stream, dzs_ctx** out) {
   B.diag = (double*)(a + pl.o_diag);
   B.convert = a + pl.o_convert;
   if (cudaMemset(B.n, 0, 16) != cudaSuccess || cudaMemset(B.err, 0, 16) != cudaSuccess ||
-      cudaMemset(B.counters, 0, 8 * 16) != cudaSuccess) {
+      cudaMemset(B.counters, 0, 8 * 32) != cudaSuccess) {
     cudaFree(c->arena);
     delete c;
     return fail(nullptr, DZS_ECUDA, "arena init");
@@ -447,7 +449,7 @@ dzs_status dzs_ics(dzs_ctx* c) {
   dzs_status s = guard(c);
   if (s) return s;
   if (c->cap != c->N0) return fail(c, DZS_EINVAL, "dzs_ics needs capacity n1d^3");
-  CK(cudaMemsetAsync(c->B.counters, 0, 8 * 16, c->stream));
+  CK(cudaMemsetAsync(c->B.counters, 0, 8 * 32, c->stream));
   CK(cudaMemsetAsync(c->B.err, 0, 16, c->stream));
   c->drained = 0;
   launch_ics(c);
@@ -1115,6 +1117,50 @@ dzs_status dzs_get_counters(dzs_ctx* c, uint64_t out[9]) {
   out[6] = ctr[7];
   out[7] = ctr[12];
   out[8] = ctr[13];
+  return DZS_OK;
+}
+
+dzs_status dzs_get_walk_counters(dzs_ctx* c, uint64_t out[4]) {
+  dzs_status s = guard(c);
+  if (s) return s;
+  if (!out) return fail(c, DZS_EINVAL, "out is NULL");
+  CK(cudaStreamSynchronize(c->stream));
+  uint64_t ctr[16];
+  CK(cudaMemcpy(ctr, c->B.counters, sizeof ctr, cudaMemcpyDeviceToHost));
+  out[0] = ctr[4];
+  out[1] = ctr[5];
+  out[2] = ctr[12];
+  out[3] = ctr[13];
+  return DZS_OK;
+}
+
+dzs_status dzs_walk_lists(dzs_ctx* c, int64_t* first, int64_t* count, int64_t* list_len, size_t cap,
+                          size_t* ngroups) {
+  dzs_status s = guard(c);
+  if (s) return s;
+  if (!ngroups) return fail(c, DZS_EINVAL, "ngroups is NULL");
+  CK(cudaStreamSynchronize(c->stream));
+  uint64_t ng = 0;
+  CK(cudaMemcpy(&ng, c->B.counters + 2, sizeof ng, cudaMemcpyDeviceToHost));
+  *ngroups = (size_t)ng;
+  if (!first && !count && !list_len) return DZS_OK;
+  if (cap < ng) return fail(c, DZS_EINVAL, "cap is below the number of walk groups");
+  std::vector<int32_t> gidx(ng), glen(ng);
+  std::vector<dzs::Node> nodes;
+  if (ng) {
+    CK(cudaMemcpy(gidx.data(), c->B.groups, 4 * ng, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(glen.data(), c->B.wlen, 4 * ng, cudaMemcpyDeviceToHost));
+    int32_t maxi = 0;
+    for (int32_t g : gidx) maxi = g > maxi ? g : maxi;
+    nodes.resize((size_t)maxi + 1);
+    CK(cudaMemcpy(nodes.data(), c->B.nodes, sizeof(dzs::Node) * nodes.size(), cudaMemcpyDeviceToHost));
+  }
+  for (uint64_t g = 0; g < ng; ++g) {
+    const dzs::Node& nd = nodes[gidx[g]];
+    if (first) first[g] = nd.start;
+    if (count) count[g] = nd.count;
+    if (list_len) list_len[g] = glen[g];
+  }
   return DZS_OK;
 }
 

@@ -61,7 +61,12 @@ __device__ __forceinline__ cplx<R> cmul(cplx<R> a, cplx<R> b) {
   return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
 }
 
-inline int grid_for(int64_t n, int threads = kThreads, int cap = 152 * 16) {
+// streaming multiprocessors of the current device (queried once per device)
+int sm_count();
+
+// blocks for n items: one per `threads` items, at most `per_sm` per SM
+inline int grid_for(int64_t n, int threads = kThreads, int per_sm = 16) {
+  const int64_t cap = (int64_t)per_sm * sm_count();
   int64_t b = (n + threads - 1) / threads;
   if (b < 1) b = 1;
   return (int)(b < cap ? b : cap);
@@ -116,6 +121,7 @@ struct Buffers {
   void* wpm = nullptr;           // real [cap]: G m / s^2 per particle (walk, lattice units)
   void* wph = nullptr;           // real [cap]: spline radius per particle (lattice units)
   void* wnh = nullptr;           // real [node cap]: node spline radius (lattice units)
+  int32_t* wlen = nullptr;       // [cap]: interaction-list length of each walk group (last walk)
   int32_t* group_head = nullptr; // [cap]
   // PM
   void* rho = nullptr;    // real [M^3]
@@ -129,8 +135,10 @@ struct Buffers {
   // device scalars
   int32_t* n = nullptr;          // particle count
   uint32_t* err = nullptr;       // error word
-  // [16]: 0 ring head, 1 records dropped, 2 groups, 3 nodes, 4 pair evaluations,
-  // 6 walk work counter, 8..11 diagnostics integer sums
+  // [32]: 0 ring head, 1 records dropped, 2 groups, 3 nodes, 4 listed pairs
+  // (list entries x group particles), 5 in-range pairs (0 < r < r_cut),
+  // 6 walk work counter, 7 deepest walk stack, 8..11 diagnostics integer sums,
+  // 12 walk node tests, 13 walk rounds, 14 a_min^2, 15 scratch
   uint64_t* counters = nullptr;
   double* diag = nullptr;        // [8 + blocks] diagnostics partials
   void* convert = nullptr;       // double [3][cap] conversion scratch

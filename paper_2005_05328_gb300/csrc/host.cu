@@ -156,4 +156,16 @@ void compute_tables(const dzs_params& P, Tables& T) {
   T.power_amp = P.sigma8 * P.sigma8 / s2;
 }
 
+int sm_count() {
+  static int cache[256] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return 1;
+  if (cache[dev] <= 0) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) return 1;
+    cache[dev] = n;
+  }
+  return cache[dev];
+}
+
 }  // namespace dzs

@@ -387,6 +387,9 @@ extern "C" dzs_status dzs_morton_sort_noalloc(const uint32_t* d_u, size_t n, uin
     base = g_scratch_dev[dev];
   }
   if (n == 0) return DZS_OK;
+  // an error left pending by earlier work on this thread is not ours to
+  // report or to clear: refuse before launching anything
+  if (cudaPeekAtLastError() != cudaSuccess) return DZS_ECUDA;
   cudaStream_t st = (cudaStream_t)cuda_stream;
   char* b = (char*)base;
   uint64_t* keyA = (uint64_t*)b;
@@ -400,8 +403,12 @@ extern "C" dzs_status dzs_morton_sort_noalloc(const uint32_t* d_u, size_t n, uin
   // totals, so nothing left over from a previous call is used
   const int nb = (int)((n + kTile - 1) / kTile);
   uint32_t* rowtot = hist + (int64_t)kDigits * nb;
+  // each launch is checked with cudaPeekAtLastError (a launch error is sticky
+  // for this call's own launches only: nothing was pending before them)
   k_set_count<<<1, 1, 0, st>>>(count, (int32_t)n);
+  if (cudaPeekAtLastError() != cudaSuccess) return DZS_ECUDA;
   k_keys<<<grid_for((int64_t)n), kThreads, 0, st>>>(count, (int64_t)n, d_u, keyA);
+  if (cudaPeekAtLastError() != cudaSuccess) return DZS_ECUDA;
   uint64_t *kin = keyA, *kout = keyB;
   uint32_t *vin = valA, *vout = valB;
   for (int pass = 0; pass < 8; ++pass) {
@@ -409,10 +416,11 @@ extern "C" dzs_status dzs_morton_sort_noalloc(const uint32_t* d_u, size_t n, uin
     k_hist<<<nb, kSortThreads, 0, st>>>(kin, count, shift, hist, nb);
     k_scan_rows<<<kDigits, 1024, 0, st>>>(hist, nb, rowtot);
     k_scatter<<<nb, kSortThreads, 0, st>>>(kin, vin, kout, vout, count, shift, hist, nb, rowtot, pass == 0);
+    if (cudaPeekAtLastError() != cudaSuccess) return DZS_ECUDA;
     std::swap(kin, kout);
     std::swap(vin, vout);
   }
   if (cudaMemcpyAsync(d_perm, vin, 4 * n, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return DZS_ECUDA;
   if (d_keys && cudaMemcpyAsync(d_keys, kin, 8 * n, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return DZS_ECUDA;
-  return cudaGetLastError() == cudaSuccess ? DZS_OK : DZS_ECUDA;
+  return DZS_OK;
 }

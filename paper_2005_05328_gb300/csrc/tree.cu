@@ -368,9 +368,9 @@ void launch_tree(dzs_ctx* c) {
   k_tree_nodes<<<(unsigned)ntiles, kTreeTile, 0, c->stream>>>(B.n, c->cap, B.key, B.u, info, tcount, ntiles,
                                                               B.lvl_count, B.cell_start, c->logM, c->P.leaf_bucket,
                                                               B.nodes, cfirst, B.parent, B.arrive, B.groups);
-  k_tree_link<<<grid_for(c->node_cap, kThreads, 152 * 8), kThreads, 0, c->stream>>>(B.lvl_count, B.nodes, cfirst,
+  k_tree_link<<<grid_for(c->node_cap, kThreads, 8), kThreads, 0, c->stream>>>(B.lvl_count, B.nodes, cfirst,
                                                                                      B.parent);
-  k_tree_up_all<<<grid_for(c->node_cap, kThreads, 152 * 8), kThreads, 0, c->stream>>>(
+  k_tree_up_all<<<grid_for(c->node_cap, kThreads, 8), kThreads, 0, c->stream>>>(
       B.lvl_count, c->cap, B.u, B.k, B.nodes, B.nsum, c->node_cap, B.parent, B.arrive);
 }
 

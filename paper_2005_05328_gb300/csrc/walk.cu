@@ -141,13 +141,14 @@ __device__ __forceinline__ void inv_and_r(double r2, double& r, double& ir) {
 
 template <class R>
 __device__ __forceinline__ void pair(const Entry<R>& E, R he, uint32_t xi, uint32_t yi, uint32_t zi, R hi,
-                                     const WalkConst<R>& C, R& ax, R& ay, R& az) {
+                                     const WalkConst<R>& C, R& ax, R& ay, R& az, unsigned& nin) {
   R dx = (R)(int32_t)(E.x - xi);
   R dy = (R)(int32_t)(E.y - yi);
   R dz = (R)(int32_t)(E.z - zi);
   // the self pair has dx = 0: the tiny bias keeps its term finite and exactly 0
   R r2 = dx * dx + dy * dy + dz * dz + (R)1e-20;
   if (r2 < C.rcut2) {
+    nin += r2 >= (R)0.5;  // distinct lattice points are >= 1 apart
     R r, ir;
     inv_and_r(r2, r, ir);
     R h = he > hi ? he : hi;
@@ -172,16 +173,16 @@ __device__ __forceinline__ void pair(const Entry<R>& E, R he, uint32_t xi, uint3
 template <class R>
 __device__ __forceinline__ void eval_list(const WalkSmem<R>& sm, int w, int len, int sub, int S, bool active,
                                           uint32_t xi, uint32_t yi, uint32_t zi, R hi, const WalkConst<R>& C,
-                                          R& ax, R& ay, R& az) {
+                                          R& ax, R& ay, R& az, unsigned& nin) {
   if (!active) return;
   int e = sub;
   for (; e + S < len; e += 2 * S) {
     Entry<R> E0 = sm.e[w][e], E1 = sm.e[w][e + S];
     R h0 = sm.h[w][e], h1 = sm.h[w][e + S];
-    pair(E0, h0, xi, yi, zi, hi, C, ax, ay, az);
-    pair(E1, h1, xi, yi, zi, hi, C, ax, ay, az);
+    pair(E0, h0, xi, yi, zi, hi, C, ax, ay, az, nin);
+    pair(E1, h1, xi, yi, zi, hi, C, ax, ay, az, nin);
   }
-  if (e < len) pair(sm.e[w][e], sm.h[w][e], xi, yi, zi, hi, C, ax, ay, az);
+  if (e < len) pair(sm.e[w][e], sm.h[w][e], xi, yi, zi, hi, C, ax, ay, az, nin);
 }
 
 template <class R>
@@ -249,13 +250,14 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(
     const int32_t* __restrict__ groups, const uint64_t* __restrict__ counters, unsigned int* __restrict__ next,
     const Node* __restrict__ nodes, const R* __restrict__ nh, int64_t cap, const uint32_t* __restrict__ u,
     const Entry<R>* __restrict__ pm, const R* __restrict__ ph, R* __restrict__ p, R* __restrict__ g, WalkConst<R> C,
-    uint32_t* __restrict__ err, unsigned long long* __restrict__ pairs) {
+    uint32_t* __restrict__ err, unsigned long long* __restrict__ pairs, int32_t* __restrict__ wlen) {
   extern __shared__ unsigned char smem_raw[];
   WalkSmem<R>& sm = *reinterpret_cast<WalkSmem<R>*>(smem_raw);
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   const int64_t ngroups = (int64_t)counters[2];
   unsigned long long npairs = 0;
+  unsigned nin = 0;  // pairs in range (0 < r < r_cut) evaluated by this lane
   int maxtop = 0;  // deepest stack use of this warp (diagnostic)
   unsigned long long ntests = 0, nrounds = 0;  // node tests and traversal rounds (diagnostic)
   const int flush_at = kList - 32 * (C.B > 1 ? C.B : 1) - 32;
@@ -284,7 +286,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(
       }
       R ax = 0, ay = 0, az = 0;
       if (C.tree) {
-        int top = 0, len = 0;
+        int top = 0, len = 0, glen = 0;
         if (C.front > 0 && glevel >= C.front) {
           // the nodes of the 27 cells around the group's depth-f cell, each once
           const int f = C.front, D = 1 << f;
@@ -429,8 +431,9 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(
             for (int q0 = 0; q0 < bc; q0 += 32) {
               if (len + 32 > kList) {
                 __syncwarp();
-                eval_list(sm, w, len, sub, S, active, xi, yi, zi, hi, C, ax, ay, az);
+                eval_list(sm, w, len, sub, S, active, xi, yi, zi, hi, C, ax, ay, az, nin);
                 npairs += (active && sub == 0) ? (unsigned long long)len : 0ull;
+                glen += len;
                 len = 0;
                 __syncwarp();
               }
@@ -446,15 +449,18 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(
             }
           }
           if (len > flush_at) {
-            eval_list(sm, w, len, sub, S, active, xi, yi, zi, hi, C, ax, ay, az);
+            eval_list(sm, w, len, sub, S, active, xi, yi, zi, hi, C, ax, ay, az, nin);
             npairs += (active && sub == 0) ? (unsigned long long)len : 0ull;
+            glen += len;
             len = 0;
             __syncwarp();
           }
         }
         __syncwarp();
-        eval_list(sm, w, len, sub, S, active, xi, yi, zi, hi, C, ax, ay, az);
+        eval_list(sm, w, len, sub, S, active, xi, yi, zi, hi, C, ax, ay, az, nin);
         npairs += (active && sub == 0) ? (unsigned long long)len : 0ull;
+        glen += len;
+        if (c0 == 0 && lane == 0) wlen[gi] = glen;
         __syncwarp();
         // combine the S partial sums of each particle: fixed shuffle tree
         // within each run of S lanes (deterministic for a given group size)
@@ -482,8 +488,13 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(
       }
     }
   }
-  for (int o = 16; o > 0; o >>= 1) npairs += __shfl_down_sync(0xffffffffu, npairs, o);
+  unsigned long long nin64 = nin;
+  for (int o = 16; o > 0; o >>= 1) {
+    npairs += __shfl_down_sync(0xffffffffu, npairs, o);
+    nin64 += __shfl_down_sync(0xffffffffu, nin64, o);
+  }
   if (lane == 0 && npairs) atomicAdd(pairs, npairs);
+  if (lane == 0 && nin64) atomicAdd(pairs + 1, nin64);
   if (lane == 0) atomicMax(pairs + 3, (unsigned long long)maxtop);
   if (lane == 0) atomicAdd(pairs + 8, ntests);
   if (lane == 0) atomicAdd(pairs + 9, nrounds);
@@ -540,7 +551,7 @@ void walk_impl(dzs_ctx* c, bool tree, bool close_kick, int step) {
     const int64_t cells = (int64_t)1 << (3 * C.front);
     c->launches += 1;
     cudaMemsetAsync(c->B.iscan, 0xff, sizeof(int32_t) * cells, c->stream);
-    k_front_fill<<<grid_for(cells, kThreads, 152 * 4), kThreads, 0, c->stream>>>(c->B.lvl_count, c->B.nodes, C.front,
+    k_front_fill<<<grid_for(cells, kThreads, 4), kThreads, 0, c->stream>>>(c->B.lvl_count, c->B.nodes, C.front,
                                                                                c->B.iscan);
   }
   size_t sm = sizeof(WalkSmem<R>);
@@ -558,7 +569,7 @@ void walk_impl(dzs_ctx* c, bool tree, bool close_kick, int step) {
   cudaMemsetAsync(next, 0, sizeof(unsigned int), c->stream);
   k_walk<R><<<grid, kWarps * 32, sm, c->stream>>>(c->B.groups, c->B.counters, next, c->B.nodes, nh, c->cap, c->B.u,
                                                   pm, ph, (R*)c->B.p, (R*)c->B.g, C, c->B.err,
-                                                  (unsigned long long*)(c->B.counters + 4));
+                                                  (unsigned long long*)(c->B.counters + 4), c->B.wlen);
 }
 
 }  // namespace

@@ -112,3 +112,12 @@ def test_struct_layouts_match_the_header(tmp_path, dzs):
         want += [ctypes.sizeof(cls)] + [getattr(cls, f[0]).offset for f in cls._fields_]
     want += [dzs.RECORD_DTYPE.itemsize]
     assert got == want
+
+
+def test_noalloc_sort_source_allocates_nothing():
+    """the allocation-free sort's entry point calls no allocating CUDA routine"""
+    import re
+    src = open(os.path.join(ROOT, "paper_2005_05328_gb300", "csrc", "sort.cu")).read()
+    body = src[src.index('extern "C" dzs_status dzs_morton_sort_noalloc'):]
+    body = body[:body.index("\n}\n") + 3]
+    assert not re.search(r"cudaMalloc|cudaFree|cudaMallocAsync|cudaHostAlloc|new |malloc\(", body)

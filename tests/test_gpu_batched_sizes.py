@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 
 import oracle as O
+from kick_parity import half_step_momentum_error, momentum_bound_fp64, momentum_sum_check
 
 pytestmark = pytest.mark.gpu
 
@@ -103,11 +104,16 @@ def test_full_step_3x2a_fp64(dzs):
         ctx.step(1)
         s = ctx.state()
         r = ctx.drain()
+        d = ctx.diagnostics()
     assert np.array_equal(np.sort(r["id"]), np.sort(rec["id"]))
     assert np.array_equal(s["id"], so["id"]) and np.array_equal(s["k"], so["k"])
     du = (s["u"].astype(np.int64) - so["u"].astype(np.int64) + 2 ** 31) % TWO32 - 2 ** 31
     assert np.abs(du).max() <= 1
     assert gerr(s["g"], so["g"]).max() <= 1e-6
+    assert half_step_momentum_error(P, 50, s, so).max() <= 1e-12
+    ok, worst = momentum_bound_fp64(P, 50, s, so)
+    assert ok, worst
+    assert momentum_sum_check(d, s, so, P) == (True, True)
 
 
 def splitmix64(state):

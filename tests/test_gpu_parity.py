@@ -17,6 +17,7 @@ import numpy as np
 import pytest
 
 import oracle as O
+from kick_parity import half_step_momentum_error, momentum_bound_fp64, momentum_sum_check
 
 pytestmark = pytest.mark.gpu
 
@@ -248,6 +249,12 @@ def test_kick_drift_records(dzs, precision):
         assert np.all(np.abs(du) <= bound)
     assert np.array_equal(np.sort(r["id"]), np.sort(rec["id"]))
     assert np.array_equal(s["fl"], so["fl"])
+    # the opening kick of every particle (not only the crossing ones):
+    # p_{n+1/2} = p_n + K(a_n, a_{n+1/2}) g_n; FP32 rounds p, g K1 and the sum
+    K1 = O.tables(P)["kick1"][60]
+    scale = np.abs(st["p"]) + np.abs(st["g"]) * K1
+    ptol = 1e-13 if precision == 1 else 3e-7
+    assert np.all(np.abs(s["p"] - so["p"]) <= ptol * scale + 1e-300), np.abs(s["p"] - so["p"]).max()
     ro, rg = rec[np.argsort(rec["id"])], r[np.argsort(r["id"])]
     tol = 1e-12 if precision == 1 else 1e-6
     assert np.allclose(rg["a_cross"], ro["a_cross"], rtol=tol)
@@ -273,9 +280,40 @@ def test_full_step_fp64(dzs, upto):
     du = (s["u"].astype(np.int64) - so["u"].astype(np.int64) + 2 ** 31) % TWO32 - 2 ** 31
     assert np.abs(du).max() <= 1
     assert gerr(s["g"], so["g"]).max() <= 1e-6
+    # momenta after the closing kick: the half-step momenta agree to rounding,
+    # the full momenta within rounding + K2 |dg|
+    assert half_step_momentum_error(P, upto, s, so).max() <= 1e-12
+    ok, worst = momentum_bound_fp64(P, upto, s, so)
+    assert ok, worst
     od = O.diagnostics(P, so["u"], so["p"], so["k"])
     assert d[0] == od[0] and d[7] == od[7]
     assert np.allclose(d[4:7], od[4:7], rtol=1e-12)
+    assert momentum_sum_check(d, s, so, P) == (True, True)
+
+
+@pytest.mark.parametrize("upto", [20, 75])
+def test_full_step_fp32(dzs, upto):
+    """FP32 state and forces: the oracle steps the FP32-rounded state; merge
+    membership, masses and ids agree exactly, accelerations within the FP32
+    bound, half-step momenta within a few float roundings"""
+    st = oracle_run(SMALL, upto)
+    st = dict(st, p=st["p"].astype(np.float32).astype(np.float64), g=st["g"].astype(np.float32).astype(np.float64))
+    P = oparams(**SMALL)
+    so, rec = O.step(P, upto, st)
+    with dzs.Context(**dict(SMALL, precision=0)) as ctx:
+        ctx.set_state(st, upto)
+        ctx.step(1)
+        s = ctx.state()
+        r = ctx.drain()
+        d = ctx.diagnostics()
+    assert np.array_equal(np.sort(r["id"]), np.sort(rec["id"]))
+    assert np.array_equal(s["id"], so["id"]) and np.array_equal(s["k"], so["k"])
+    assert np.percentile(gerr(s["g"], so["g"]), 99.9) <= 1e-4
+    assert half_step_momentum_error(P, upto, s, so).max() <= 2e-6
+    od = O.diagnostics(P, so["u"], so["p"], so["k"])
+    assert d[0] == od[0] and d[7] == od[7]
+    own, _ = momentum_sum_check(d, s, so, P)
+    assert own
 
 
 def test_steps_are_deterministic(dzs):
