@@ -15,7 +15,10 @@
  *   - the walk is done per group (node with <= G particles whose parent has
  *     more, or a leaf) against the group's cube: skip a node whose cube is
  *     farther than r_cut from the group cube, open it when the cubes touch or
- *     l_n >= theta d(COM_n, group cube), else use its monopole;
+ *     l_n >= theta d(COM_n, group cube), else use its monopole; a monopole or
+ *     a particle of an opened leaf that lies farther than r_cut from the group
+ *     cube is left off the list (it is farther than r_cut from every particle
+ *     of the group, so its short-range force on them is zero);
  *   - softening: cubic-spline kernel of Plummer-equivalent eps
  *     (spline radius 2.8 eps), eps = eps0 k^(1/3) (Sec. 2.2 rescaling),
  *     pair softening max(eps_i, eps_j), node softening = max over members;
@@ -213,6 +216,16 @@ static void list_push(llist* l, const uint32_t x[3], uint32_t k, uint32_t kmax) 
 
 static int64_t iabs64(int64_t v) { return v < 0 ? -v : v; }
 
+/* squared lattice distance from point x to the group cube (centre cg, side lg) */
+static uint64_t point_cube_d2(const uint32_t x[3], const uint64_t cg[3], uint64_t lg) {
+  uint64_t d2 = 0;
+  for (int ax = 0; ax < 3; ++ax) {
+    int64_t dm = iabs64((int64_t)(int32_t)(uint32_t)((uint64_t)x[ax] - cg[ax])) - (int64_t)(lg / 2);
+    if (dm > 0) d2 += (uint64_t)dm * (uint64_t)dm;
+  }
+  return d2;
+}
+
 /* depth-first walk of node idx for the group cube (cg, lg) */
 static void walk_rec(const dzso_params* P, const otree* t, int64_t idx, const uint64_t cg[3],
                      uint64_t lg, double rcut_lat2, int64_t n, const uint32_t* u,
@@ -233,12 +246,17 @@ static void walk_rec(const dzso_params* P, const otree* t, int64_t idx, const ui
   if (!touch && (double)dist2 > rcut_lat2) return; /* every pair beyond r_cut */
   int open = touch || ((double)nd->side >= P->theta * sqrt((double)dcom2));
   if (!open) {
-    list_push(out, nd->com, (uint32_t)nd->K, nd->kmax);
+    /* a monopole farther than r_cut from the group cube acts on none of the
+     * group's particles: not listed */
+    if ((double)dcom2 <= rcut_lat2) list_push(out, nd->com, (uint32_t)nd->K, nd->kmax);
     return;
   }
   if (nd->child < 0) {
     for (int64_t i = nd->s; i < nd->e; ++i) {
       uint32_t x[3] = {u[i], u[(size_t)n + i], u[2 * (size_t)n + i]};
+      /* likewise a particle of an opened leaf farther than r_cut from the
+       * group cube (same distance rule as the node skip) */
+      if ((double)point_cube_d2(x, cg, lg) > rcut_lat2) continue;
       list_push(out, x, k[i], k[i]);
     }
     return;

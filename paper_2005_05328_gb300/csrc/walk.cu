@@ -17,20 +17,30 @@
 // at the root.  Per node:
 //   skip   the node's cube is farther than r_cut from the group cube;
 //   open   the cubes touch, or l_n >= theta d(COM_n, group cube);
-//   accept otherwise: the monopole (COM, mass, softening) joins the list.
-// Opened leaves put their particles on the list.  Cube gaps and COM distances
-// are exact integers.  The FP64 comparisons that define skip and open
-// ((double)gap^2 <= r_cut^2, (double)l >= theta sqrt((double)d^2)) are
-// monotone in the integer d^2, so the host turns each into an exact integer
-// threshold once per context: the walk compares integers only and builds the
-// same interaction set as the CPU reference, with no FP64 in the walk.
-// The list lives in shared memory; when it fills, all 32 lanes evaluate it:
-// a group of c particles gets S = floor(32 / c) lanes per particle, each lane
-// summing every S-th entry, combined by a fixed shuffle tree (the result is
-// deterministic).  Pair force: softened 1/r^3 times
-// T(r) = erfc(x) + (2/sqrt(pi)) x exp(-x^2), x = r / 2 r_s, zero at r = 0 and
-// r >= r_cut.  FP32 evaluates T = exp(-x^2) Q(x) with a fitted polynomial
-// (gen_split_poly.py, relative error 3.3e-7); FP64 calls erfc and exp.
+//   accept otherwise: the monopole (COM, mass, softening) joins the list,
+//          unless its COM lies farther than r_cut from the group cube.
+// Opened leaves put their particles on the list, except those farther than
+// r_cut from the group cube (such a monopole or particle acts on no particle
+// of the group).  Cube gaps and COM distances are exact integers.  The FP64
+// comparisons that define skip and open ((double)gap^2 <= r_cut^2,
+// (double)l >= theta sqrt((double)d^2)) are monotone in the integer d^2, so
+// the host turns each into an exact integer threshold once per context: the
+// walk compares integers only (FP32 sums decide unless within 2^-20 of a
+// threshold, where the uint64 sum decides) and builds the same interaction
+// set as the CPU reference, with no FP64 in the traversal.
+// The list lives in shared memory and is evaluated between rounds, when it
+// holds more than 236 entries (a round adds at most 32 monopoles and the
+// leaves that fit; leaves that do not fit wait on the stack).  A group of c
+// particles puts every lane to work: lane -> particle m = lane mod c, the
+// S_m lanes of particle m each taking every S_m-th entry.  Entries are taken
+// 32 at a time: a cheap pass tests r < r_cut into a bit mask, then only the
+// pairs in range get the force arithmetic (the warp iterates as often as its
+// busiest lane has pairs in range); the lanes of a particle are combined by a
+// fixed shuffle tree (the result is deterministic).  Pair force: softened
+// 1/r^3 times T(r) = erfc(x) + (2/sqrt(pi)) x exp(-x^2), x = r / 2 r_s, zero
+// at r = 0 and r >= r_cut.  FP32 evaluates T = exp(-x^2) Q(x) with a fitted
+// polynomial (gen_split_poly.py, relative error 3.3e-7); FP64 calls erfc and
+// exp.
 #include <cmath>
 
 #include "common.cuh"
@@ -38,10 +48,9 @@
 namespace dzs {
 namespace {
 
-// shared memory sets the occupancy (7 blocks of 4 warps per SM, 72 registers):
-// stack 512 entries (deepest use measured 308; an overflow sets an error
-// bit), list 300 entries (a round adds at most 32 monopoles and 32 B leaf
-// particles, so a list above 300 - 32 B - 32 is evaluated before the next)
+// shared memory sets the occupancy (7 blocks of 4 warps per SM, 72 registers
+// in FP32): stack 512 entries (deepest use measured 308; an overflow sets an
+// error bit), list 300 entries
 constexpr int kWarps = 4;
 constexpr int kStack = 512;
 constexpr int kList = 300;
@@ -139,50 +148,132 @@ __device__ __forceinline__ void inv_and_r(double r2, double& r, double& ir) {
   ir = 1.0 / r;
 }
 
+// squared lattice distance of entry E from particle (xi, yi, zi), from the
+// exact int32 minimum-image offsets
 template <class R>
-__device__ __forceinline__ void pair(const Entry<R>& E, R he, uint32_t xi, uint32_t yi, uint32_t zi, R hi,
-                                     const WalkConst<R>& C, R& ax, R& ay, R& az, unsigned& nin) {
-  R dx = (R)(int32_t)(E.x - xi);
-  R dy = (R)(int32_t)(E.y - yi);
-  R dz = (R)(int32_t)(E.z - zi);
-  // the self pair has dx = 0: the tiny bias keeps its term finite and exactly 0
-  R r2 = dx * dx + dy * dy + dz * dz + (R)1e-20;
-  if (r2 < C.rcut2) {
-    nin += r2 >= (R)0.5;  // distinct lattice points are >= 1 apart
-    R r, ir;
-    inv_and_r(r2, r, ir);
-    R h = he > hi ? he : hi;
-    R fac = (r >= h) ? ir * ir * ir : spline_fac(r, h);
-    R sfac;
-    if (sizeof(R) == 4 && C.poly) {
-      const float t = fmaf((float)r, (float)C.tcoef, -1.0f);
-      float q = kSplitPoly[11];
+__device__ __forceinline__ R entry_r2(const Entry<R>& E, uint32_t xi, uint32_t yi, uint32_t zi, R& dx, R& dy,
+                                      R& dz) {
+  dx = (R)(int32_t)(E.x - xi);
+  dy = (R)(int32_t)(E.y - yi);
+  dz = (R)(int32_t)(E.z - zi);
+  return dx * dx + dy * dy + dz * dz;
+}
+
+// force of one entry at offset (dx, dy, dz), 0 < r^2 < r_cut^2 (the caller
+// has tested the range)
+template <class R>
+__device__ __forceinline__ void pair_force(R dx, R dy, R dz, R r2, R m, R he, R hi, const WalkConst<R>& C, R& ax,
+                                           R& ay, R& az) {
+  R r, ir;
+  inv_and_r(r2, r, ir);
+  const R h = he > hi ? he : hi;
+  const R fac = (r >= h) ? ir * ir * ir : spline_fac(r, h);
+  R sfac;
+  if (sizeof(R) == 4 && C.poly) {
+    const float t = fmaf((float)r, (float)C.tcoef, -1.0f);
+    float q = kSplitPoly[11];
 #pragma unroll
-      for (int i = 10; i >= 0; --i) q = fmaf(q, t, kSplitPoly[i]);
-      sfac = (R)(ex2_approx((float)r2 * (float)C.nl2) * q);
-    } else {
-      sfac = split_factor(r * C.inv2rs, C.poly);
-    }
-    R f = E.m * fac * sfac;
-    ax += f * dx;
-    ay += f * dy;
-    az += f * dz;
+    for (int i = 10; i >= 0; --i) q = fmaf(q, t, kSplitPoly[i]);
+    sfac = (R)(ex2_approx((float)r2 * (float)C.nl2) * q);
+  } else {
+    sfac = split_factor(r * C.inv2rs, C.poly);
   }
+  const R f = m * fac * sfac;
+  ax += f * dx;
+  ay += f * dy;
+  az += f * dz;
 }
 
 template <class R>
-__device__ __forceinline__ void eval_list(const WalkSmem<R>& sm, int w, int len, int sub, int S, bool active,
-                                          uint32_t xi, uint32_t yi, uint32_t zi, R hi, const WalkConst<R>& C,
-                                          R& ax, R& ay, R& az, unsigned& nin) {
-  if (!active) return;
-  int e = sub;
-  for (; e + S < len; e += 2 * S) {
-    Entry<R> E0 = sm.e[w][e], E1 = sm.e[w][e + S];
-    R h0 = sm.h[w][e], h1 = sm.h[w][e + S];
-    pair(E0, h0, xi, yi, zi, hi, C, ax, ay, az, nin);
-    pair(E1, h1, xi, yi, zi, hi, C, ax, ay, az, nin);
+__device__ __forceinline__ void pair_in_range(const Entry<R>& E, R he, uint32_t xi, uint32_t yi, uint32_t zi, R hi,
+                                              const WalkConst<R>& C, R& ax, R& ay, R& az) {
+  R dx, dy, dz;
+  const R r2 = entry_r2(E, xi, yi, zi, dx, dy, dz);
+  pair_force(dx, dy, dz, r2, E.m, he, hi, C, ax, ay, az);
+}
+
+// Evaluate the list [0, len) for this lane's particle: the lane takes every
+// Sm-th entry from `sub`.  Entries are taken 32 at a time: a cheap pass tests
+// each against r_cut (and r > 0: the self pair) into a bit mask, then the lane
+// evaluates only the set bits, so the force arithmetic runs for in-range pairs
+// only and the warp iterates as often as its busiest lane has pairs in range.
+template <class R, bool kMasked>
+__device__ __forceinline__ void eval_list(const WalkSmem<R>& sm, int w, int len, int sub, int Sm, uint32_t xi,
+                                          uint32_t yi, uint32_t zi, R hi, const WalkConst<R>& C, R& ax, R& ay,
+                                          R& az, unsigned& nin) {
+  if (!kMasked) {
+    // most entries in range (a group cube small against r_cut): one pass,
+    // the force arithmetic guarded by the range test
+    int e = sub;
+    for (; e + Sm < len; e += 2 * Sm) {  // two entries per iteration (independent chains)
+      const Entry<R> E0 = sm.e[w][e], E1 = sm.e[w][e + Sm];
+      const R h0 = sm.h[w][e], h1 = sm.h[w][e + Sm];
+      R dx0, dy0, dz0, dx1, dy1, dz1;
+      const R r0 = entry_r2(E0, xi, yi, zi, dx0, dy0, dz0);
+      const R r1 = entry_r2(E1, xi, yi, zi, dx1, dy1, dz1);
+      if (r0 < C.rcut2 && r0 > (R)0) {
+        ++nin;
+        pair_force(dx0, dy0, dz0, r0, E0.m, h0, hi, C, ax, ay, az);
+      }
+      if (r1 < C.rcut2 && r1 > (R)0) {
+        ++nin;
+        pair_force(dx1, dy1, dz1, r1, E1.m, h1, hi, C, ax, ay, az);
+      }
+    }
+    if (e < len) {
+      const Entry<R> E0 = sm.e[w][e];
+      R dx, dy, dz;
+      const R r2 = entry_r2(E0, xi, yi, zi, dx, dy, dz);
+      if (r2 < C.rcut2 && r2 > (R)0) {
+        ++nin;
+        pair_force(dx, dy, dz, r2, E0.m, sm.h[w][e], hi, C, ax, ay, az);
+      }
+    }
+    return;
   }
-  if (e < len) pair(sm.e[w][e], sm.h[w][e], xi, yi, zi, hi, C, ax, ay, az, nin);
+  const int nk = sub < len ? (len - sub + Sm - 1) / Sm : 0;
+  const int nkmax = __reduce_max_sync(0xffffffffu, (unsigned)nk);
+  for (int kb = 0; kb < nkmax; kb += 32) {
+    unsigned mask = 0;
+    const int kend = nk - kb < 32 ? nk - kb : 32;
+    const Entry<R>* ep = &sm.e[w][sub + kb * Sm];
+#pragma unroll 4
+    for (int k = 0; k < kend; ++k) {
+      R dx, dy, dz;
+      const R r2 = entry_r2(ep[k * Sm], xi, yi, zi, dx, dy, dz);
+      mask |= (r2 < C.rcut2 && r2 > (R)0) ? (1u << k) : 0u;
+    }
+    nin += __popc(mask);
+    while (__any_sync(0xffffffffu, mask != 0u)) {
+      if (mask) {
+        const int k = __ffs(mask) - 1;
+        mask &= mask - 1u;
+        const int e = sub + (kb + k) * Sm;
+        pair_in_range(sm.e[w][e], sm.h[w][e], xi, yi, zi, hi, C, ax, ay, az);
+      }
+    }
+  }
+}
+
+// lattice point within r_cut of the group cube (centre cg, half side hg): the
+// skip rule of the node test applied to a point (its distance to the cube)
+template <class R>
+__device__ __forceinline__ bool near_group(uint32_t px, uint32_t py, uint32_t pz, const uint32_t (&cg)[3],
+                                           uint32_t hg, const WalkConst<R>& C) {
+  const uint32_t pp[3] = {px, py, pz};
+  uint32_t dv[3];
+  float d2f = 0.f;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int32_t ms = (int32_t)(pp[a] - cg[a]);
+    const uint32_t mc = ms < 0 ? 0u - (uint32_t)ms : (uint32_t)ms;
+    const uint32_t dm = mc > hg ? mc - hg : 0u;
+    dv[a] = dm;
+    d2f = fmaf((float)dm, (float)dm, d2f);
+  }
+  if (d2f <= C.skip_lo) return true;
+  if (d2f >= C.skip_hi) return false;
+  return exact_d2(dv) <= C.skip_d2;
 }
 
 template <class R>
@@ -245,8 +336,11 @@ __global__ void k_front_fill(const int32_t* __restrict__ lvl, const Node* __rest
   }
 }
 
-template <class R>
-__global__ void __launch_bounds__(kWarps * 32) k_walk(
+// kMasked: evaluate lists with the range-masked pass (pays off when many
+// listed entries lie beyond r_cut of a given particle: groups not small
+// against r_cut), else with one range-guarded pass
+template <class R, bool kMasked>
+__global__ void __launch_bounds__(kWarps * 32, sizeof(R) == 4 ? 7 : 5) k_walk(
     const int32_t* __restrict__ groups, const uint64_t* __restrict__ counters, unsigned int* __restrict__ next,
     const Node* __restrict__ nodes, const R* __restrict__ nh, int64_t cap, const uint32_t* __restrict__ u,
     const Entry<R>* __restrict__ pm, const R* __restrict__ ph, R* __restrict__ p, R* __restrict__ g, WalkConst<R> C,
@@ -256,34 +350,28 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   const int64_t ngroups = (int64_t)counters[2];
-  unsigned long long npairs = 0;
-  unsigned nin = 0;  // pairs in range (0 < r < r_cut) evaluated by this lane
+  unsigned npairs = 0;  // listed pairs of this warp (lane 0 counts them; < 2^32 per warp)
+  unsigned nin = 0;               // pairs in range (0 < r < r_cut) evaluated by this lane
   int maxtop = 0;  // deepest stack use of this warp (diagnostic)
-  unsigned long long ntests = 0, nrounds = 0;  // node tests and traversal rounds (diagnostic)
-  const int flush_at = kList - 32 * (C.B > 1 ? C.B : 1) - 32;
+  unsigned ntests = 0, nrounds = 0;  // node tests and traversal rounds of this warp (diagnostic)
   for (;;) {
-    int64_t gi = 0;
-    if (lane == 0) gi = atomicAdd(next, 1u);
+    int gi = 0;
+    if (lane == 0) gi = (int)atomicAdd(next, 1u);
     gi = __shfl_sync(0xffffffffu, gi, 0);
-    if (gi >= ngroups) break;
+    if ((int64_t)gi >= ngroups) break;
     const Node gn = nodes[groups[gi]];
     const int glevel = gn.meta & 0xff;
     const uint32_t hg = 1u << (31 - glevel);  // half side of the group cube
+    const uint32_t cg[3] = {gn.cx, gn.cy, gn.cz};
     for (int c0 = 0; c0 < gn.count; c0 += 32) {
       const int cnt = gn.count - c0 < 32 ? gn.count - c0 : 32;
-      // S = floor(32 / c) lanes per particle (c * S <= 32 lanes busy)
-      const int S = 32 / cnt;
-      const int mine = lane / S, sub = lane - mine * S;
-      const int64_t i = (int64_t)gn.start + c0 + mine;
-      const bool active = mine < cnt;
-      uint32_t xi = 0, yi = 0, zi = 0;
-      R hi = 0;
-      if (active) {
-        xi = u[i];
-        yi = u[cap + i];
-        zi = u[2 * cap + i];
-        hi = ph[i];
-      }
+      // every lane works: lane -> particle m = lane mod cnt, the Sm lanes of
+      // particle m (sub = 0 .. Sm - 1) each take every Sm-th list entry
+      const int m = lane % cnt, sub = lane / cnt;
+      const int Sm = 32 / cnt + (m < 32 % cnt ? 1 : 0);
+      const int i = gn.start + c0 + m;
+      const uint32_t xi = u[i], yi = u[cap + i], zi = u[2 * cap + i];
+      const R hi = ph[i];
       R ax = 0, ay = 0, az = 0;
       if (C.tree) {
         int top = 0, len = 0, glen = 0;
@@ -309,7 +397,20 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(
           top = 1;
         }
         __syncwarp();
+        // evaluate and empty the list (warp-uniform)
+#define DZS_WALK_FLUSH()                                                     \
+  do {                                                                       \
+    __syncwarp();                                                            \
+    eval_list<R, kMasked>(sm, w, len, sub, Sm, xi, yi, zi, hi, C, ax, ay, az, nin); \
+    if (lane == 0) npairs += (unsigned)len * (unsigned)cnt;                  \
+    glen += len;                                                             \
+    len = 0;                                                                 \
+    __syncwarp();                                                            \
+  } while (0)
         while (top > 0) {
+          // the list is evaluated only here, between rounds (a round adds at
+          // most 32 monopoles and the leaves that fit; the others wait)
+          if (len > kList - 64) DZS_WALK_FLUSH();
           const int npop = top < 32 ? top : 32;
           ntests += npop;
           nrounds += 1;
@@ -328,7 +429,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(
             bool touch = true;
             uint32_t gp[3], dmv[3];
             float d2f = 0.f, c2f = 0.f;
-            const uint32_t cn[3] = {nd.cx, nd.cy, nd.cz}, cg[3] = {gn.cx, gn.cy, gn.cz};
+            const uint32_t cn[3] = {nd.cx, nd.cy, nd.cz};
             const uint32_t cm[3] = {nd.comx, nd.comy, nd.comz};
             const uint32_t hn = nlevel == 0 ? 0u : (1u << (31 - nlevel));
 #pragma unroll
@@ -361,15 +462,18 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(
                 else if (c2f < C.open_hi[nlevel])
                   open = exact_d2(dmv) <= C.open_d2[nlevel];
               }
-              if (!open)
-                acc = true;
-              else if (nd.child < 0)
+              if (!open) {
+                // an accepted monopole farther than r_cut from the group cube
+                // acts on none of its particles: not listed
+                acc = c2f <= C.skip_lo || (c2f < C.skip_hi && exact_d2(dmv) <= C.skip_d2);
+              } else if (nd.child < 0) {
                 leaf = true;
-              else
+              } else {
                 inner = true;
+              }
             }
           }
-          // accepted monopoles
+          // accepted monopoles (at most 32 this round)
           unsigned am = __ballot_sync(0xffffffffu, acc);
           if (acc) {
             int pos = len + __popc(am & lt);
@@ -395,11 +499,30 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(
           for (int q = 0; q < nch; ++q) sm.stack[w][top + ex + q] = nd.child + q;
           top += tot;
           maxtop = top > maxtop ? top : maxtop;
-          // particles of opened small leaves, copied cooperatively: item t of
-          // the round belongs to the lane whose inclusive end first exceeds t
+          // particles of opened small leaves, copied cooperatively (item t of
+          // the round belongs to the lane whose inclusive end first exceeds t);
+          // a particle farther than r_cut from the group cube acts on none of
+          // the group's particles and is not listed
+          // leaves whose particles do not fit in the list this round go back
+          // on the stack (the inclusive ends grow with the lane, so the ones
+          // that fit are a prefix); after the next evaluation they fit
           int lc = (leaf && nd.count <= C.B) ? nd.count : 0;
           int incl = warp_incl_scan<R>(lc, lane);
-          int totl = __shfl_sync(0xffffffffu, incl, 31);
+          const int room = kList - len;
+          const bool defer = lc > 0 && incl > room;
+          const unsigned dm = __ballot_sync(0xffffffffu, defer);
+          if (dm) {
+            if (top + __popc(dm) > kStack) {
+              if (lane == 0) atomicOr(err, kErrStack);
+            } else if (defer) {
+              sm.stack[w][top + __popc(dm & lt)] = ni;
+            }
+            top += top + __popc(dm) > kStack ? 0 : __popc(dm);
+            if (defer) lc = 0;
+          }
+          // items of the leaves that stay: the largest inclusive end within
+          // the room (lanes past a deferred leaf carry its items in incl)
+          const int totl = (int)__reduce_max_sync(0xffffffffu, (unsigned)(incl <= room ? incl : 0));
           int lstart = leaf ? nd.start : 0;
           for (int b0 = 0; b0 < totl; b0 += 32) {
             int t = b0 + lane;
@@ -412,14 +535,22 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(
             int send = __shfl_sync(0xffffffffu, incl, src);
             int scnt = __shfl_sync(0xffffffffu, lc, src);
             int sst = __shfl_sync(0xffffffffu, lstart, src);
+            bool take = false;
+            Entry<R> E;
+            int64_t j = 0;
             if (t < totl) {
-              int64_t j = (int64_t)sst + (t - (send - scnt));
-              Entry<R> E = pm[j];
-              sm.e[w][len + t] = E;
-              sm.h[w][len + t] = ph[j];
+              j = (int64_t)sst + (t - (send - scnt));
+              E = pm[j];
+              take = near_group(E.x, E.y, E.z, cg, hg, C);
             }
+            const unsigned tm = __ballot_sync(0xffffffffu, take);
+            if (take) {
+              const int pos = len + __popc(tm & lt);
+              sm.e[w][pos] = E;
+              sm.h[w][pos] = ph[j];
+            }
+            len += __popc(tm);
           }
-          len += totl;
           __syncwarp();
           // big leaves (depth 21, more than B particles): stream through
           unsigned bm = __ballot_sync(0xffffffffu, leaf && nd.count > C.B);
@@ -429,45 +560,36 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(
             int bs = __shfl_sync(0xffffffffu, nd.start, src);
             int bc = __shfl_sync(0xffffffffu, nd.count, src);
             for (int q0 = 0; q0 < bc; q0 += 32) {
-              if (len + 32 > kList) {
-                __syncwarp();
-                eval_list(sm, w, len, sub, S, active, xi, yi, zi, hi, C, ax, ay, az, nin);
-                npairs += (active && sub == 0) ? (unsigned long long)len : 0ull;
-                glen += len;
-                len = 0;
-                __syncwarp();
+              if (len + 32 > kList) DZS_WALK_FLUSH();
+              bool take = false;
+              Entry<R> E;
+              int64_t j = 0;
+              if (q0 + lane < bc) {
+                j = (int64_t)bs + q0 + lane;
+                E = pm[j];
+                take = near_group(E.x, E.y, E.z, cg, hg, C);
               }
-              int mm = bc - q0 < 32 ? bc - q0 : 32;
-              if (lane < mm) {
-                int64_t j = (int64_t)bs + q0 + lane;
-                Entry<R> E = pm[j];
-                sm.e[w][len + lane] = E;
-                sm.h[w][len + lane] = ph[j];
+              const unsigned tm = __ballot_sync(0xffffffffu, take);
+              if (take) {
+                const int pos = len + __popc(tm & lt);
+                sm.e[w][pos] = E;
+                sm.h[w][pos] = ph[j];
               }
-              len += mm;
-              __syncwarp();
+              len += __popc(tm);
             }
-          }
-          if (len > flush_at) {
-            eval_list(sm, w, len, sub, S, active, xi, yi, zi, hi, C, ax, ay, az, nin);
-            npairs += (active && sub == 0) ? (unsigned long long)len : 0ull;
-            glen += len;
-            len = 0;
             __syncwarp();
           }
         }
-        __syncwarp();
-        eval_list(sm, w, len, sub, S, active, xi, yi, zi, hi, C, ax, ay, az, nin);
-        npairs += (active && sub == 0) ? (unsigned long long)len : 0ull;
-        glen += len;
+        DZS_WALK_FLUSH();
+#undef DZS_WALK_FLUSH
         if (c0 == 0 && lane == 0) wlen[gi] = glen;
-        __syncwarp();
-        // combine the S partial sums of each particle: fixed shuffle tree
-        // within each run of S lanes (deterministic for a given group size)
-        for (int o = 1; o < S; o <<= 1) {
-          const bool in = sub + o < S;
-          R tx = __shfl_down_sync(0xffffffffu, ax, o), ty = __shfl_down_sync(0xffffffffu, ay, o);
-          R tz = __shfl_down_sync(0xffffffffu, az, o);
+        // combine the Sm partial sums of each particle: fixed shuffle tree over
+        // its lanes m, m + cnt, m + 2 cnt, ... (deterministic for a given cnt)
+        const int smax = 32 / cnt + (32 % cnt ? 1 : 0);
+        for (int o = 1; o < smax; o <<= 1) {
+          const bool in = (sub & (2 * o - 1)) == 0 && sub + o < Sm;
+          R tx = __shfl_down_sync(0xffffffffu, ax, o * cnt), ty = __shfl_down_sync(0xffffffffu, ay, o * cnt);
+          R tz = __shfl_down_sync(0xffffffffu, az, o * cnt);
           if (in) {
             ax += tx;
             ay += ty;
@@ -475,7 +597,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(
           }
         }
       }
-      if (active && sub == 0) {
+      if (sub == 0) {
         R gx = g[i] + ax, gy = g[cap + i] + ay, gz = g[2 * cap + i] + az;
         g[i] = gx;
         g[cap + i] = gy;
@@ -489,15 +611,12 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(
     }
   }
   unsigned long long nin64 = nin;
-  for (int o = 16; o > 0; o >>= 1) {
-    npairs += __shfl_down_sync(0xffffffffu, npairs, o);
-    nin64 += __shfl_down_sync(0xffffffffu, nin64, o);
-  }
-  if (lane == 0 && npairs) atomicAdd(pairs, npairs);
+  for (int o = 16; o > 0; o >>= 1) nin64 += __shfl_down_sync(0xffffffffu, nin64, o);
+  if (lane == 0 && npairs) atomicAdd(pairs, (unsigned long long)npairs);
   if (lane == 0 && nin64) atomicAdd(pairs + 1, nin64);
   if (lane == 0) atomicMax(pairs + 3, (unsigned long long)maxtop);
-  if (lane == 0) atomicAdd(pairs + 8, ntests);
-  if (lane == 0) atomicAdd(pairs + 9, nrounds);
+  if (lane == 0) atomicAdd(pairs + 8, (unsigned long long)ntests);
+  if (lane == 0) atomicAdd(pairs + 9, (unsigned long long)nrounds);
 }
 
 template <class R>
@@ -554,20 +673,25 @@ void walk_impl(dzs_ctx* c, bool tree, bool close_kick, int step) {
     k_front_fill<<<grid_for(cells, kThreads, 4), kThreads, 0, c->stream>>>(c->B.lvl_count, c->B.nodes, C.front,
                                                                                c->B.iscan);
   }
+  // the range-masked evaluation when the walk groups of a uniform particle
+  // set (leaves of ~B particles, side ~2 spacings) are at least r_cut / 2 wide
+  const double spacing = c->P.box / c->P.n1d;
+  const bool masked = 4.0 * spacing >= c->rcut;
+  auto kern = masked ? k_walk<R, true> : k_walk<R, false>;
   size_t sm = sizeof(WalkSmem<R>);
-  static bool attr_done[2] = {false, false};
-  if (!attr_done[sizeof(R) == 8]) {
-    cudaFuncSetAttribute(k_walk<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    attr_done[sizeof(R) == 8] = true;
+  static bool attr_done[2][2] = {{false, false}, {false, false}};
+  if (!attr_done[sizeof(R) == 8][masked]) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    attr_done[sizeof(R) == 8][masked] = true;
   }
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk<R>, kWarps * 32, sm);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWarps * 32, sm);
   int nsm = 0;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->dev);
   int grid = (per_sm > 0 ? per_sm : 1) * (nsm > 0 ? nsm : 1);
   unsigned int* next = (unsigned int*)(c->B.counters + 6);
   cudaMemsetAsync(next, 0, sizeof(unsigned int), c->stream);
-  k_walk<R><<<grid, kWarps * 32, sm, c->stream>>>(c->B.groups, c->B.counters, next, c->B.nodes, nh, c->cap, c->B.u,
+  kern<<<grid, kWarps * 32, sm, c->stream>>>(c->B.groups, c->B.counters, next, c->B.nodes, nh, c->cap, c->B.u,
                                                   pm, ph, (R*)c->B.p, (R*)c->B.g, C, c->B.err,
                                                   (unsigned long long*)(c->B.counters + 4), c->B.wlen);
 }

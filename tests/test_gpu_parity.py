@@ -342,3 +342,25 @@ def test_full_run_records_every_particle_once(dzs):
     assert sorted(rec["id"].tolist()) == list(range(16 ** 3))
     assert d[0] == 16 ** 3  # mass conserved through every merge
     assert n < 16 ** 3  # DZS merged particles outside the lightcone
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+@pytest.mark.parametrize("upto", [0, 80])
+def test_accel_coarse_mesh(dzs, precision, upto):
+    """mesh spacing twice the particle spacing (as the 512^3 configuration):
+    r_cut = 11.25 Mpc/h spans many walk groups, so the walk evaluates its lists
+    in the single range-guarded pass; parity as in the other force tests"""
+    kw = dict(n1d=16, mesh=16, box=32.0, merge_level=2)
+    st = oracle_run(kw, upto)
+    P = oparams(**kw)
+    want = O.accel(P, st["u"], st["k"])
+    with dzs.Context(**dict(kw, precision=precision)) as ctx:
+        ctx.set_state(st, upto)
+        got = ctx.accel()
+        cnt = ctx.counters()
+    e = gerr(got, want)
+    if precision == 1:
+        assert e.max() <= 1e-9, e.max()
+        assert cnt[2] == O.interaction_count(P, st["u"], st["k"])
+    else:
+        assert np.percentile(e, 99.9) <= 1e-4, np.percentile(e, 99.9)

@@ -40,8 +40,9 @@ def hand_list_force(cs, P, u, k, names, i):
     rs = P.rs_cells * box / P.mesh
     rcut = P.rcut_rs * rs
     entries = []  # (lattice position, K, kmax)
+    unlisted = {tuple(int(round(c / box * TWO32)) for c in pt) for pt in cs.get("unlisted_points_A", [])}
     for t in range(u.shape[1]):
-        if names[t] in cs["expected_particle_clusters_A"]:
+        if names[t] in cs["expected_particle_clusters_A"] and tuple(int(v) for v in u[:, t]) not in unlisted:
             entries.append((u[:, t].astype(np.int64), int(k[t]), int(k[t])))
     for m in cs["expected_monopoles_A"]:
         entries.append((np.array([int(round(c / box * TWO32)) for c in m["com"]], np.int64), m["K"], m["kmax"]))
@@ -88,4 +89,5 @@ def test_hand_list_distinguishes_the_plausible_mistakes():
     alt2 = dict(cs)
     alt2["expected_particle_clusters_A"] = ["A", "B", "S"]
     alt2["expected_list_length_A"] = cs["expected_list_length_A"] - 3
+    alt2["unlisted_points_A"] = []
     assert np.abs(hand_list_force(alt2, P, u, k, names, s) - base).max() > 1e-3 * np.abs(base).max()

@@ -19,7 +19,7 @@ def clusters():
     c = {}
     c["A"] = [p for p in itertools.product(T3, T3, T3) if p not in ((20.375, 20.375, 20.25), (20.375, 20.375, 20.375))]
     c["B"] = list(itertools.product((20.625, 20.875), repeat=3))
-    c["R"] = [(19.0, 20.25, z) for z in T3]
+    c["R"] = [(19.0, 20.25, z) for z in T3] + [(16.25, 23.75, 23.75)]
     c["S"] = [(22.5, y, z) for y in (20.125, 20.375) for z in (20.125, 20.375)]
     c["Q"] = [(x, y, z) for y in (24.25, 25.75) for x in T3 for z in (20.125, 20.375)]
     c["Q2"] = [(24.25, y, z) for y in T3 for z in T3] + [(25.25, y, 20.25) for y in T3]
