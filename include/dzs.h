@@ -105,7 +105,8 @@ typedef struct {
   uint64_t seed;        /* IC white-noise seed */
   int32_t precision;    /* DZS_FP32 | DZS_FP64 force arithmetic */
   int32_t device;       /* CUDA device ordinal */
-  uint64_t lc_capacity; /* lightcone ring records; 0 = N0 (never overflows) */
+  uint64_t lc_capacity; /* lightcone ring records; 0 = N0 (never overflows); a smaller
+                          ring makes dzs_step check each step's records first */
   int32_t dzs_criterion; /* DZS_CRIT_GEOMETRIC: l/D < theta_dzs (Sec. 2.2.1);
                            DZS_CRIT_DYNAMICAL: Eq. 2 with d -> D of Eq. 3 */
   int32_t reserved_;     /* must be 0 */
@@ -149,7 +150,13 @@ DZS_API dzs_status dzs_create(const dzs_params* p, void* cuda_stream, dzs_ctx** 
 DZS_API dzs_status dzs_ics(dzs_ctx* c);
 
 /* Enqueue up to nsteps full KDK steps (DZS_STAGE_ALL), stopping at a = 1.
- * *steps_done (nullable) receives the number enqueued. */
+ * *steps_done (nullable) receives the number enqueued.  With a lightcone ring
+ * smaller than N0 (lc_capacity), each step first counts the records it will
+ * write (a dry run of its kick, drift and crossing test; synchronises); if
+ * they do not fit in the ring's room, the step is not started and
+ * DZS_EOVERFLOW is returned (recoverable: drain, then call dzs_step again,
+ * which resumes with that step; *steps_done counts the steps enqueued before
+ * it).  With the default ring nothing is checked and no record is ever lost. */
 DZS_API dzs_status dzs_step(dzs_ctx* c, int32_t nsteps, int32_t* steps_done);
 
 /* Run the stages in stage_mask of the current step in stage order, without
@@ -458,6 +465,26 @@ DZS_API dzs_status dzs_morton_sort_noalloc(const uint32_t* d_u, size_t n, uint32
  * device memory for the duration of the call and restores the current device.
  * Synchronous; DZS_EINVAL for reps < 1, DZS_EDEVICE / DZS_ECUDA on failure. */
 DZS_API dzs_status dzs_measure_fp32_peaks(int32_t device, int32_t reps, double* fma_tflops, double* sfu_gops);
+
+/* Twin-run integration accuracy (paper Sec. 3.2, the particle-by-particle
+ * comparison of twin simulations with and without DZS): for the particles
+ * inside the lightcone (not crossed) in both contexts a and b, matched by id,
+ * the minimum-image distance of their positions divided by the softening
+ * length h = L / n1d / 40, histogrammed by the nbins + 1 increasing edges
+ * (host, in units of h): counts[k] (host, nbins) receives the pairs with
+ * edges[k] <= dx / h < edges[k + 1]; *matched (nullable) the number of pairs,
+ * *max_ratio (nullable) the largest dx / h.  FP64, correctly rounded, fixed
+ * order: exact counts.  Both contexts on one device with the same n1d and box;
+ * allocates a scratch of 4 n1d^3 bytes for the call; synchronises both streams.
+ * DZS_EINVAL on bad arguments, DZS_ESTATE without particle states. */
+DZS_API dzs_status dzs_twin_displacement(dzs_ctx* a, dzs_ctx* b, const double* edges, int32_t nbins,
+                                         uint64_t* counts, uint64_t* matched, double* max_ratio);
+
+/* Test hook (no counterpart in the paper): make the k-th device allocation
+ * the library attempts from now on fail as if the device were out of memory
+ * (k = 0 disables).  Host-side only: no GPU fault is involved.  The failing
+ * call returns DZS_ENOMEM and frees what it had allocated. */
+DZS_API void dzs_debug_fail_alloc(int32_t k);
 
 /* Message of the last failure on this context (valid until the next call).
  * c may be NULL (then: the last dzs_create failure of this thread). */

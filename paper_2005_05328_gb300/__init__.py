@@ -33,7 +33,7 @@ PK_SHOT = 1
 EXPORTED = ["dzs_params_default", "dzs_footprint_bytes", "dzs_create", "dzs_ics", "dzs_step",
             "dzs_run_stages", "dzs_lightcone_drain", "dzs_destroy", "dzs_get_count", "dzs_get_state",
             "dzs_set_state", "dzs_accel", "dzs_merge_only", "dzs_diagnostics", "dzs_get_tables",
-            "dzs_get_mesh", "dzs_get_counters", "dzs_get_walk_counters", "dzs_walk_lists", "dzs_measure_fp32_peaks", "dzs_set_profiling", "dzs_get_profile",
+            "dzs_get_mesh", "dzs_get_counters", "dzs_get_walk_counters", "dzs_walk_lists", "dzs_measure_fp32_peaks", "dzs_debug_fail_alloc", "dzs_twin_displacement", "dzs_set_profiling", "dzs_get_profile",
             "dzs_morton_sort_noalloc", "dzs_checkpoint_bytes", "dzs_checkpoint", "dzs_restore",
             "dzs_step_until", "dzs_observe_enable", "dzs_observe_add_records", "dzs_skymap_get",
             "dzs_lcdensity_get", "dzs_skymap_alm", "dzs_power_spectrum", "dzs_serve", "dzs_fof", "dzs_last_error"]
@@ -121,7 +121,9 @@ def load(path: str = LIB_PATH):
         "dzs_get_tables": [vp, vp, vp, vp, vp, vp, vp], "dzs_get_mesh": [vp, i32, vp],
         "dzs_get_counters": [vp, vp], "dzs_get_walk_counters": [vp, vp],
         "dzs_walk_lists": [vp, vp, vp, vp, sz, C.POINTER(sz)],
-        "dzs_measure_fp32_peaks": [i32, i32, C.POINTER(C.c_double), C.POINTER(C.c_double)], "dzs_set_profiling": [vp, i32], "dzs_get_profile": [vp, vp, vp],
+        "dzs_measure_fp32_peaks": [i32, i32, C.POINTER(C.c_double), C.POINTER(C.c_double)],
+        "dzs_debug_fail_alloc": [i32],
+        "dzs_twin_displacement": [vp, vp, vp, i32, vp, vp, C.POINTER(C.c_double)], "dzs_set_profiling": [vp, i32], "dzs_get_profile": [vp, vp, vp],
         "dzs_checkpoint_bytes": [vp, C.POINTER(sz)], "dzs_checkpoint": [vp, vp, sz, C.POINTER(sz)],
         "dzs_restore": [vp, vp, sz],
         "dzs_step_until": [vp, i32, C.POINTER(Halt), C.POINTER(i32), C.POINTER(i32), C.POINTER(C.c_double)],
@@ -137,6 +139,7 @@ def load(path: str = LIB_PATH):
         f.restype = C.c_int
     L.dzs_morton_sort_noalloc.argtypes = [vp, sz, vp, vp, vp]
     L.dzs_morton_sort_noalloc.restype = C.c_int
+    L.dzs_debug_fail_alloc.restype = None
     L.dzs_last_error.argtypes = [vp]
     L.dzs_last_error.restype = C.c_char_p
     _lib = L
@@ -292,6 +295,23 @@ def dzs_measure_fp32_peaks(device=0, reps=5):
     if st != DZS_OK:
         raise RuntimeError("dzs_measure_fp32_peaks failed with status %d" % st)
     return f.value, s.value
+
+
+def dzs_debug_fail_alloc(k):
+    """test hook: the k-th device allocation from now on fails (0: off)"""
+    load().dzs_debug_fail_alloc(int(k))
+
+
+def dzs_twin_displacement(ha, hb, edges):
+    """counts per bin of dx / h (edges in units of h), matched pairs, largest
+    dx / h, of the uncrossed twin particles of two contexts"""
+    edges = np.ascontiguousarray(edges, np.float64)
+    nb = len(edges) - 1
+    counts = np.zeros(nb, np.uint64)
+    matched = np.zeros(1, np.uint64)
+    mx = C.c_double(0)
+    _check(load().dzs_twin_displacement(ha, hb, _ptr(edges), nb, _ptr(counts), _ptr(matched), C.byref(mx)), ha)
+    return counts, int(matched[0]), mx.value
 
 
 def dzs_walk_lists(h):

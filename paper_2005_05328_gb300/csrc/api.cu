@@ -12,6 +12,8 @@
 #include <string>
 #include <vector>
 
+#include <atomic>
+
 #include "common.cuh"
 
 using namespace dzs;
@@ -154,6 +156,21 @@ struct Plan {
     cudaError_t e_ = (call);                                                       \
     if (e_ != cudaSuccess) return fail(c, DZS_ECUDA, #call, cudaGetErrorString(e_)); \
   } while (0)
+
+// host-side allocation-failure injection (tests): the k-th device
+// allocation from now on fails as if the device were out of memory
+std::atomic<int> g_fail_alloc{0};
+
+cudaError_t dev_alloc(void** ptr, size_t bytes) {
+  int k = g_fail_alloc.load();
+  while (k > 0) {
+    if (g_fail_alloc.compare_exchange_weak(k, k - 1)) {
+      if (k == 1) return cudaErrorMemoryAllocation;
+      break;
+    }
+  }
+  return cudaMalloc(ptr, bytes);
+}
 
 dzs_status fail(dzs_ctx* c, dzs_status s, const char* what, const char* detail = nullptr) {
   std::string m = what ? what : "";
@@ -358,7 +375,7 @@ dzs_status dzs_create(const dzs_params* p, void* cuda_stream, dzs_ctx** out) {
     delete c;
     return fail(nullptr, DZS_EDEVICE, "cudaSetDevice");
   }
-  cudaError_t e = cudaMalloc((void**)&c->arena, pl.total);
+  cudaError_t e = dev_alloc((void**)&c->arena, pl.total);
   if (e != cudaSuccess) {
     delete c;
     return fail(nullptr, DZS_ENOMEM, "device arena", cudaGetErrorString(e));
@@ -510,6 +527,30 @@ dzs_status dzs_run_stages(dzs_ctx* c, uint32_t mask) {
   return DZS_OK;
 }
 
+// Before a full step: a ring smaller than N0 may not hold the step's records
+// (with ring_cap >= N0 it always does: the records pending plus those still to
+// come are distinct particles, each recorded once).  A dry run of the step's
+// kick, drift and crossing test counts them (synchronises); if they do not
+// fit, the step is not started and the caller drains and steps again.
+dzs_status ring_guard(dzs_ctx* c) {
+  if (c->ring_cap >= (size_t)c->N0 || c->step >= c->P.nsteps) return DZS_OK;
+  unsigned long long* cnt = (unsigned long long*)(c->B.counters + 18);
+  CK(cudaMemsetAsync(cnt, 0, sizeof(uint64_t), c->stream));
+  launch_count_crossings(c, c->step, cnt);
+  uint64_t ctr[19];
+  CK(cudaMemcpyAsync(ctr, c->B.counters, sizeof ctr, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  const uint64_t pending = ctr[0] - c->drained;
+  const uint64_t room = c->ring_cap > pending ? c->ring_cap - pending : 0;
+  if (ctr[18] > room) {
+    char buf[160];
+    snprintf(buf, sizeof buf, "lightcone ring full: step %d would record %llu, room %llu; drain and step again",
+             (int)c->step, (unsigned long long)ctr[18], (unsigned long long)room);
+    return fail(c, DZS_EOVERFLOW, buf);
+  }
+  return DZS_OK;
+}
+
 dzs_status dzs_step(dzs_ctx* c, int32_t nsteps, int32_t* steps_done) {
   dzs_status s = guard(c);
   if (s) return s;
@@ -517,8 +558,12 @@ dzs_status dzs_step(dzs_ctx* c, int32_t nsteps, int32_t* steps_done) {
   if (nsteps < 0) return fail(c, DZS_EINVAL, "nsteps < 0");
   int done = 0;
   while (done < nsteps && c->step < c->P.nsteps) {
-    s = dzs_run_stages(c, DZS_STAGE_ALL);
-    if (s) return s;
+    s = ring_guard(c);
+    if (!s) s = dzs_run_stages(c, DZS_STAGE_ALL);
+    if (s) {
+      if (steps_done) *steps_done = done;
+      return s;
+    }
     ++done;
   }
   if (steps_done) *steps_done = done;
@@ -543,7 +588,8 @@ dzs_status dzs_step_until(dzs_ctx* c, int32_t max_steps, const dzs_halt* h, int3
   if (ratio) *ratio = r;
   int done = 0;
   while (done < max_steps && c->step < c->P.nsteps) {
-    s = dzs_run_stages(c, DZS_STAGE_ALL);
+    s = ring_guard(c);
+    if (!s) s = dzs_run_stages(c, DZS_STAGE_ALL);
     if (s) return s;
     ++done;
     if (steps_done) *steps_done = done;
@@ -875,12 +921,12 @@ dzs_status dzs_observe_enable(dzs_ctx* c, const dzs_observe* o) {
   t.box = c->P.box;
   if (t.nside) {
     const size_t b = 8 * (size_t)(12 * t.nside * t.nside);
-    if (cudaMalloc((void**)&t.sky, b) != cudaSuccess) return fail(c, DZS_ENOMEM, "sky map");
+    if (dev_alloc((void**)&t.sky, b) != cudaSuccess) return fail(c, DZS_ENOMEM, "sky map");
     CK(cudaMemset(t.sky, 0, b));
   }
   if (t.mesh) {
     const size_t b = 8 * (size_t)t.mesh * t.mesh * t.mesh;
-    if (cudaMalloc((void**)&t.grid, b) != cudaSuccess) {
+    if (dev_alloc((void**)&t.grid, b) != cudaSuccess) {
       if (t.sky) cudaFree(t.sky);
       return fail(c, DZS_ENOMEM, "3D lightcone grid");
     }
@@ -941,7 +987,7 @@ dzs_status dzs_skymap_alm(dzs_ctx* c, int32_t lmax, double* cl, double* alm) {
     if (c->sht_work) CK(cudaFree(c->sht_work));
     c->sht_work = nullptr;
     c->sht_bytes = 0;
-    if (cudaMalloc(&c->sht_work, need) != cudaSuccess) return fail(c, DZS_ENOMEM, "harmonic-analysis scratch");
+    if (dev_alloc(&c->sht_work, need) != cudaSuccess) return fail(c, DZS_ENOMEM, "harmonic-analysis scratch");
     c->sht_bytes = need;
   }
   double2* d_alm = nullptr;
@@ -1118,6 +1164,55 @@ dzs_status dzs_get_counters(dzs_ctx* c, uint64_t out[9]) {
   out[7] = ctr[12];
   out[8] = ctr[13];
   return DZS_OK;
+}
+
+void dzs_debug_fail_alloc(int32_t k) { g_fail_alloc.store(k > 0 ? k : 0); }
+
+dzs_status dzs_twin_displacement(dzs_ctx* a, dzs_ctx* b, const double* edges, int32_t nbins, uint64_t* counts,
+                                 uint64_t* matched, double* max_ratio) {
+  dzs_status s = guard(a);
+  if (s) return s;
+  s = guard(b);
+  if (s) return s;
+  if (!edges || nbins < 1 || !counts) return fail(a, DZS_EINVAL, "edges, nbins or counts");
+  for (int k = 0; k < nbins; ++k)
+    if (!(edges[k] < edges[k + 1])) return fail(a, DZS_EINVAL, "edges must increase");
+  if (a->dev != b->dev || a->N0 != b->N0 || a->P.box != b->P.box)
+    return fail(a, DZS_EINVAL, "twin runs must share the device, N0 and the box");
+  if (!a->have_state || !b->have_state) return fail(a, DZS_ESTATE, "no particle state");
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return fail(b, DZS_EDEVICE, "device failure");
+  const size_t bytes = 4 * (size_t)a->N0 + 8 * (size_t)(nbins + 1) + 8 * (size_t)nbins + 16 + 1024;
+  char* tmp = nullptr;
+  if (dev_alloc((void**)&tmp, bytes) != cudaSuccess) return fail(a, DZS_ENOMEM, "twin displacement scratch");
+  double* d_edges = (double*)tmp;
+  unsigned long long* d_counts = (unsigned long long*)(tmp + 8 * (size_t)(nbins + 1));
+  unsigned long long* d_stats = d_counts + nbins;
+  int32_t* map = (int32_t*)(d_stats + 2);
+  dzs_status st = DZS_OK;
+  if (cudaMemcpyAsync(d_edges, edges, 8 * (size_t)(nbins + 1), cudaMemcpyHostToDevice, a->stream) != cudaSuccess ||
+      cudaMemsetAsync(d_counts, 0, 8 * (size_t)(nbins + 2), a->stream) != cudaSuccess) {
+    st = fail(a, DZS_ECUDA, "twin displacement set-up");
+  }
+  if (!st) {
+    const double h = a->P.box / a->P.n1d / 40.0;  // softening length of Sec. 3.2
+    launch_twin_displacement(a, b, map, d_edges, nbins, h, d_counts, d_stats);
+    std::vector<unsigned long long> hc((size_t)nbins + 2);
+    if (cudaMemcpyAsync(hc.data(), d_counts, 8 * hc.size(), cudaMemcpyDeviceToHost, a->stream) != cudaSuccess ||
+        cudaStreamSynchronize(a->stream) != cudaSuccess) {
+      st = fail(a, DZS_EDEVICE, "twin displacement");
+    } else {
+      for (int k = 0; k < nbins; ++k) counts[k] = hc[k];
+      if (matched) *matched = hc[nbins];
+      if (max_ratio) {
+        const unsigned long long bits = hc[nbins + 1];
+        double v;
+        std::memcpy(&v, &bits, 8);
+        *max_ratio = v;
+      }
+    }
+  }
+  cudaFree(tmp);
+  return st;
 }
 
 dzs_status dzs_get_walk_counters(dzs_ctx* c, uint64_t out[4]) {

@@ -138,7 +138,8 @@ struct Buffers {
   // [32]: 0 ring head, 1 records dropped, 2 groups, 3 nodes, 4 listed pairs
   // (list entries x group particles), 5 in-range pairs (0 < r < r_cut),
   // 6 walk work counter, 7 deepest walk stack, 8..11 diagnostics integer sums,
-  // 12 walk node tests, 13 walk rounds, 14 a_min^2, 15 scratch
+  // 12 walk node tests, 13 walk rounds, 14 a_min^2, 15 scratch, 16 walk units,
+  // 18 crossings of the next step (ring check)
   uint64_t* counters = nullptr;
   double* diag = nullptr;        // [8 + blocks] diagnostics partials
   void* convert = nullptr;       // double [3][cap] conversion scratch
@@ -211,6 +212,9 @@ double bbks_shape(const dzs_params& P, double k);  // k^ns T(k)^2
 // launchers (each file); all enqueue on c->stream
 void launch_kick_drift(dzs_ctx* c, int step, bool kick, bool drift);
 void launch_records(dzs_ctx* c, int step);
+void launch_count_crossings(dzs_ctx* c, int step, unsigned long long* count);
+void launch_twin_displacement(dzs_ctx* a, dzs_ctx* b, int32_t* map, const double* edges, int nbins, double h,
+                              unsigned long long* counts, unsigned long long* stats);
 void launch_sort(dzs_ctx* c);
 void launch_sort_keys(dzs_ctx* c, uint64_t* ka, uint64_t* kb, uint32_t* va, uint32_t* vb, int passes);
 void launch_keys(dzs_ctx* c);

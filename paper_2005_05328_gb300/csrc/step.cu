@@ -12,23 +12,30 @@
 namespace dzs {
 namespace {
 
+__device__ __forceinline__ float kicked(float p, float g, float k) { return fmaf(g, k, p); }
+__device__ __forceinline__ double kicked(double p, double g, double k) { return fma(g, k, p); }
+
 // p += g K1; u += rint(p D 2^32 / L); crossing; key.  Grid-stride over n.
-template <class R>
+// kDry: the same kick, drift and crossing test, nothing written; the number of
+// particles that would cross is added to *count (the lightcone ring's room is
+// checked with it before a step that might overflow a small ring)
+template <class R, bool kDry>
 __global__ void k_kick_drift(const int32_t* __restrict__ d_n, int64_t cap, uint32_t* __restrict__ u,
                              R* __restrict__ p, const R* __restrict__ g, uint8_t* __restrict__ fl,
                              uint64_t* __restrict__ key, int32_t* __restrict__ now, R kick,
-                             double dlat, uint64_t r20, uint64_t r21) {
+                             double dlat, uint64_t r20, uint64_t r21, unsigned long long* __restrict__ count) {
   const int64_t n = *d_n;
+  unsigned ncross = 0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     uint32_t ub[3], ua[3];
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
-      R pj = p[ax * cap + i] + g[ax * cap + i] * kick;
-      p[ax * cap + i] = pj;
+      const R pj = kicked(p[ax * cap + i], g[ax * cap + i], kick);
+      if (!kDry) p[ax * cap + i] = pj;
       ub[ax] = u[ax * cap + i];
       long long du = __double2ll_rn((double)pj * dlat);
       ua[ax] = ub[ax] + (uint32_t)(unsigned long long)du;
-      u[ax * cap + i] = ua[ax];
+      if (!kDry) u[ax * cap + i] = ua[ax];
     }
     uint8_t f = fl[i] & (uint8_t)~kFlNow;
     int32_t crossed = 0;
@@ -40,9 +47,17 @@ __global__ void k_kick_drift(const int32_t* __restrict__ d_n, int64_t cap, uint3
         crossed = 1;
       }
     }
-    fl[i] = f;
-    now[i] = crossed;
-    key[i] = morton_key(ua[0], ua[1], ua[2]);
+    if (kDry) {
+      ncross += (unsigned)crossed;
+    } else {
+      fl[i] = f;
+      now[i] = crossed;
+      key[i] = morton_key(ua[0], ua[1], ua[2]);
+    }
+  }
+  if (kDry) {
+    for (int o = 16; o > 0; o >>= 1) ncross += __shfl_down_sync(0xffffffffu, ncross, o);
+    if ((threadIdx.x & 31) == 0 && ncross) atomicAdd(count, (unsigned long long)ncross);
   }
 }
 
@@ -166,13 +181,32 @@ void launch_kick_drift(dzs_ctx* c, int step, bool, bool) {
   int grid = grid_for(c->N0);
   int32_t* now = c->B.iscan + (c->cap + 1);  // second half of the int scratch
   if (c->fp64)
-    k_kick_drift<double><<<grid, kThreads, 0, c->stream>>>(c->B.n, c->cap, c->B.u, (double*)c->B.p,
-                                                           (const double*)c->B.g, c->B.fl, c->B.key, now,
-                                                           c->T.kick1[step], dlat, r0 * r0, r1 * r1);
+    k_kick_drift<double, false><<<grid, kThreads, 0, c->stream>>>(c->B.n, c->cap, c->B.u, (double*)c->B.p,
+                                                                  (const double*)c->B.g, c->B.fl, c->B.key, now,
+                                                                  c->T.kick1[step], dlat, r0 * r0, r1 * r1, nullptr);
   else
-    k_kick_drift<float><<<grid, kThreads, 0, c->stream>>>(c->B.n, c->cap, c->B.u, (float*)c->B.p,
-                                                          (const float*)c->B.g, c->B.fl, c->B.key, now,
-                                                          (float)c->T.kick1[step], dlat, r0 * r0, r1 * r1);
+    k_kick_drift<float, false><<<grid, kThreads, 0, c->stream>>>(c->B.n, c->cap, c->B.u, (float*)c->B.p,
+                                                                 (const float*)c->B.g, c->B.fl, c->B.key, now,
+                                                                 (float)c->T.kick1[step], dlat, r0 * r0, r1 * r1,
+                                                                 nullptr);
+}
+
+// the number of particles that step `step` would record (a dry run of its
+// kick, drift and crossing test), added to *count on the device
+void launch_count_crossings(dzs_ctx* c, int step, unsigned long long* count) {
+  c->launches += 1;
+  uint64_t r0 = c->T.rlat[step], r1 = c->T.rlat[step + 1];
+  double dlat = c->T.drift[step] * c->lat;
+  int grid = grid_for(c->N0);
+  if (c->fp64)
+    k_kick_drift<double, true><<<grid, kThreads, 0, c->stream>>>(c->B.n, c->cap, c->B.u, (double*)c->B.p,
+                                                                 (const double*)c->B.g, c->B.fl, nullptr, nullptr,
+                                                                 c->T.kick1[step], dlat, r0 * r0, r1 * r1, count);
+  else
+    k_kick_drift<float, true><<<grid, kThreads, 0, c->stream>>>(c->B.n, c->cap, c->B.u, (float*)c->B.p,
+                                                                (const float*)c->B.g, c->B.fl, nullptr, nullptr,
+                                                                (float)c->T.kick1[step], dlat, r0 * r0, r1 * r1,
+                                                                count);
 }
 
 void launch_records(dzs_ctx* c, int step) {
