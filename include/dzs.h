@@ -61,6 +61,7 @@ typedef enum {
 enum { DZS_RLC_SWEEP = 0, DZS_RLC_PHYSICAL = 1 };
 enum { DZS_FP32 = 0, DZS_FP64 = 1 };
 enum { DZS_CRIT_GEOMETRIC = 0, DZS_CRIT_DYNAMICAL = 1 };
+enum { DZS_WALK_AUTO = 0, DZS_WALK_MASKED = 1, DZS_WALK_GUARDED = 2 };
 
 /* flag bits of a particle */
 enum { DZS_FL_CROSSED = 1, DZS_FL_MERGED = 2 };
@@ -109,7 +110,11 @@ typedef struct {
                           ring makes dzs_step check each step's records first */
   int32_t dzs_criterion; /* DZS_CRIT_GEOMETRIC: l/D < theta_dzs (Sec. 2.2.1);
                            DZS_CRIT_DYNAMICAL: Eq. 2 with d -> D of Eq. 3 */
-  int32_t reserved_;     /* must be 0 */
+  int32_t walk_eval;     /* execution only (results identical): how the tree walk
+                            evaluates its lists; DZS_WALK_AUTO (0), DZS_WALK_MASKED
+                            (1: a range-test pass, then force arithmetic for the
+                            pairs within r_cut), DZS_WALK_GUARDED (2: one pass, the
+                            arithmetic guarded by the range test) */
   double alpha_dyn;      /* dynamical: merge iff D > 0 and G M l^2 / D^4 <
                             alpha_dyn a_min, a_min = smallest |g| (previous
                             step) of the particles not yet crossed; >= 0 */
@@ -330,6 +335,8 @@ typedef struct {
   double hbm_budget_bytes;
   int32_t max_active;      /* 0: no limit besides the budget */
   int32_t steps_per_slice; /* >= 1 */
+  int32_t host_threads;    /* host threads feeding the mocks; 0: min(8, hardware threads) */
+  int32_t reserved_;
   dzs_params base;         /* everything but n1d, mesh, box, sigma8, seed (capacity ignored) */
 } dzs_serve_config;
 
@@ -337,7 +344,11 @@ typedef struct {
  * out[i] belongs to req[i].  Returns DZS_OK, or the first failing status (the
  * other requests still run); a request that alone exceeds the budget gets
  * DZS_ENOMEM.  *wall_s (may be NULL) = seconds from start to the last
- * completion.  The calling thread drives the loop until every request is done. */
+ * completion.  The calling thread waits until every request is done; the
+ * mocks are created, stepped, drained and destroyed by host_threads worker
+ * threads (each admitted mock belongs to one of them; admission stays in
+ * arrival order under the shared budget), so the kernel launches of many
+ * small mocks are issued in parallel. */
 DZS_API dzs_status dzs_serve(const dzs_serve_config* cfg, const dzs_request* req, size_t n,
                              dzs_request_result* out, double* wall_s);
 

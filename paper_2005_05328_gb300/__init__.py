@@ -24,6 +24,7 @@ STATUS_NAMES = ["DZS_OK", "DZS_EINVAL", "DZS_ENOMEM", "DZS_ECUDA", "DZS_EOVERFLO
 RLC_SWEEP, RLC_PHYSICAL = 0, 1
 FP32, FP64 = 0, 1
 CRIT_GEOMETRIC, CRIT_DYNAMICAL = 0, 1
+WALK_AUTO, WALK_MASKED, WALK_GUARDED = 0, 1, 2
 FL_CROSSED, FL_MERGED = 1, 2
 STAGE_KICK_DRIFT, STAGE_SORT, STAGE_MERGE, STAGE_FORCE, STAGE_CLOSE, STAGE_ALL = 1, 2, 4, 8, 16, 31
 ACC_PM, ACC_TREE, ACC_ALL = 1, 2, 3
@@ -51,7 +52,7 @@ class Params(C.Structure):
         ("rs_cells", C.c_double), ("rcut_rs", C.c_double), ("theta", C.c_double),
         ("soft_frac", C.c_double), ("theta_dzs", C.c_double), ("buffer_cells", C.c_double),
         ("seed", C.c_uint64), ("precision", C.c_int32), ("device", C.c_int32),
-        ("lc_capacity", C.c_uint64), ("dzs_criterion", C.c_int32), ("reserved_", C.c_int32),
+        ("lc_capacity", C.c_uint64), ("dzs_criterion", C.c_int32), ("walk_eval", C.c_int32),
         ("alpha_dyn", C.c_double), ("capacity", C.c_uint64),
     ]
 
@@ -76,7 +77,7 @@ class RequestResult(C.Structure):
 
 class ServeConfig(C.Structure):
     _fields_ = [("hbm_budget_bytes", C.c_double), ("max_active", C.c_int32), ("steps_per_slice", C.c_int32),
-                ("base", Params)]
+                ("host_threads", C.c_int32), ("reserved_", C.c_int32), ("base", Params)]
 
 
 class Observe(C.Structure):
@@ -388,7 +389,7 @@ def dzs_power_spectrum(h, nbins, shot=True):
     return k, p, n
 
 
-def dzs_serve(requests, hbm_budget_bytes, max_active=0, steps_per_slice=8, **base):
+def dzs_serve(requests, hbm_budget_bytes, max_active=0, steps_per_slice=8, host_threads=0, **base):
     """requests: iterable of dicts (arrival_s, n1d, mesh, box, sigma8, seed).
     -> (status, wall seconds, list of result dicts with arrival_s and latency_s)"""
     reqs = list(requests)
@@ -397,7 +398,8 @@ def dzs_serve(requests, hbm_budget_bytes, max_active=0, steps_per_slice=8, **bas
         arr[i] = Request(float(r["arrival_s"]), int(r["n1d"]), int(r["mesh"]), float(r["box"]),
                          float(r["sigma8"]), int(r["seed"]))
     res = (RequestResult * max(1, len(reqs)))()
-    cfg = ServeConfig(float(hbm_budget_bytes), int(max_active), int(steps_per_slice), params(**base))
+    cfg = ServeConfig(float(hbm_budget_bytes), int(max_active), int(steps_per_slice), int(host_threads), 0,
+                      params(**base))
     wall = C.c_double(0)
     st = load().dzs_serve(C.byref(cfg), C.cast(arr, C.c_void_p), len(reqs), C.cast(res, C.c_void_p),
                           C.byref(wall))

@@ -53,7 +53,7 @@ const char* validate(const dzs_params* p) {
   if (p->precision != DZS_FP32 && p->precision != DZS_FP64) return "unknown precision";
   if (p->dzs_criterion != DZS_CRIT_GEOMETRIC && p->dzs_criterion != DZS_CRIT_DYNAMICAL) return "unknown dzs_criterion";
   if (!(p->alpha_dyn >= 0)) return "alpha_dyn must be >= 0";
-  if (p->reserved_ != 0) return "reserved_ must be 0";
+  if (p->walk_eval < DZS_WALK_AUTO || p->walk_eval > DZS_WALK_GUARDED) return "walk_eval must be 0, 1 or 2";
   if (p->capacity > (uint64_t)p->n1d * p->n1d * p->n1d) return "capacity exceeds n1d^3";
   return nullptr;
 }
@@ -795,6 +795,7 @@ bool same_physics(const dzs_params& a, const dzs_params& b) {
   x.device = y.device = 0;
   x.lc_capacity = y.lc_capacity = 0;
   x.capacity = y.capacity = 0;
+  x.walk_eval = y.walk_eval = 0;  // execution only
   return memcmp(&x, &y, sizeof x) == 0;
 }
 }  // namespace

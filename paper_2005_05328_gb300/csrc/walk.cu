@@ -673,10 +673,12 @@ void walk_impl(dzs_ctx* c, bool tree, bool close_kick, int step) {
     k_front_fill<<<grid_for(cells, kThreads, 4), kThreads, 0, c->stream>>>(c->B.lvl_count, c->B.nodes, C.front,
                                                                                c->B.iscan);
   }
-  // the range-masked evaluation when the walk groups of a uniform particle
-  // set (leaves of ~B particles, side ~2 spacings) are at least r_cut / 2 wide
+  // automatic: the range-masked evaluation when the walk groups of a uniform
+  // particle set (leaves of ~B particles, side ~2 spacings) are at least
+  // r_cut / 2 wide; both evaluate the same pairs in the same order
   const double spacing = c->P.box / c->P.n1d;
-  const bool masked = 4.0 * spacing >= c->rcut;
+  const bool masked = c->P.walk_eval == DZS_WALK_MASKED ||
+                      (c->P.walk_eval == DZS_WALK_AUTO && 4.0 * spacing >= c->rcut);
   auto kern = masked ? k_walk<R, true> : k_walk<R, false>;
   size_t sm = sizeof(WalkSmem<R>);
   static bool attr_done[2][2] = {{false, false}, {false, false}};

@@ -121,3 +121,12 @@ def test_noalloc_sort_source_allocates_nothing():
     body = src[src.index('extern "C" dzs_status dzs_morton_sort_noalloc'):]
     body = body[:body.index("\n}\n") + 3]
     assert not re.search(r"cudaMalloc|cudaFree|cudaMallocAsync|cudaHostAlloc|new |malloc\(", body)
+
+
+def test_autotune_cache_path_follows_the_environment(monkeypatch, tmp_path):
+    from paper_2005_05328_gb300 import autotune
+    monkeypatch.setenv("DZS_TUNE_CACHE", str(tmp_path / "x.json"))
+    assert autotune.cache_path() == str(tmp_path / "x.json")
+    assert autotune._load() == {}
+    autotune._store({"k": {"walk_eval": 1}})
+    assert autotune._load() == {"k": {"walk_eval": 1}}
