@@ -67,11 +67,12 @@ IMPL_BYTES = {
     "fft": lambda n, m3: 40.3 * m3,
 }
 
-# DRAM bytes (read + write) of one k_walk launch from an ncu capture and the
-# walk source it was taken on: reported as roofline traffic only while the
-# source is unchanged
-WALK_TRAFFIC_BYTES = None
-WALK_TRAFFIC_SRC = None
+# DRAM bytes (read + write) of one k_walk launch from an ncu capture (step 11
+# of the bench mock, profiles/ncu_k_walk_c2_128cubed_step11.md) and the walk
+# source it was taken on: reported as roofline traffic only while the source
+# is unchanged
+WALK_TRAFFIC_BYTES = 173.198080e6 + 37.207296e6
+WALK_TRAFFIC_SRC = "675183fd15c21ca2"
 
 # serving sample (Poisson stream of mock requests, sizes 32^3 .. 256^3)
 SERVE_RATE = 4.0
@@ -601,6 +602,8 @@ def main():
             "peak": fma_peak, "unit": "TFLOP/s", "frac": achieved_tf / fma_peak, "traffic": traffic,
             "peak_source": "measured: FP32 FMA-chain micro-benchmark on this GPU (dzs_measure_fp32_peaks, "
                            "best of 5, timed alone)",
+            "traffic_note": "DRAM read + write of one launch (ncu, step 11; the timed launches span steps "
+                            "W..W+K-1)",
             "flop_per_in_range_pair": FMA_FLOP_PER_PAIR, "in_range_pairs_per_launch": in_per_launch,
             "listed_pairs_per_launch": pairs / max(1, walk_calls),
             "in_range_fraction": pairs_in / max(1, pairs),
