@@ -76,10 +76,69 @@ struct __align__(8) Entry<double> {
   double m;
 };
 
+// list entry in shared memory: FP32 holds the offset from the group cube's
+// centre in lattice units, converted once when the entry is listed (a pair
+// test is then three FP32 subtractions; every listed entry lies within r_cut
+// of the cube, so the offset keeps its lattice precision to a few units);
+// FP64 holds the exact lattice position (pair offsets are exact integers)
+template <class R>
+struct LEntry;
+template <>
+struct __align__(16) LEntry<float> {
+  float x, y, z, m;
+};
+template <>
+struct __align__(8) LEntry<double> {
+  uint32_t x, y, z, pad;
+  double m;
+};
+
+// the lane's particle in the same representation
+template <class R>
+struct Pos;
+template <>
+struct Pos<float> {
+  float x, y, z;
+};
+template <>
+struct Pos<double> {
+  uint32_t x, y, z;
+};
+
+__device__ __forceinline__ LEntry<float> make_entry(uint32_t ux, uint32_t uy, uint32_t uz, float m,
+                                                    const uint32_t (&cg)[3]) {
+  LEntry<float> E;
+  E.x = (float)(int32_t)(ux - cg[0]);
+  E.y = (float)(int32_t)(uy - cg[1]);
+  E.z = (float)(int32_t)(uz - cg[2]);
+  E.m = m;
+  return E;
+}
+__device__ __forceinline__ LEntry<double> make_entry(uint32_t ux, uint32_t uy, uint32_t uz, double m,
+                                                     const uint32_t (&)[3]) {
+  LEntry<double> E;
+  E.x = ux;
+  E.y = uy;
+  E.z = uz;
+  E.pad = 0;
+  E.m = m;
+  return E;
+}
+template <class R>
+__device__ __forceinline__ Pos<R> make_pos(uint32_t x, uint32_t y, uint32_t z, const uint32_t (&cg)[3]);
+template <>
+__device__ __forceinline__ Pos<float> make_pos<float>(uint32_t x, uint32_t y, uint32_t z, const uint32_t (&cg)[3]) {
+  return Pos<float>{(float)(int32_t)(x - cg[0]), (float)(int32_t)(y - cg[1]), (float)(int32_t)(z - cg[2])};
+}
+template <>
+__device__ __forceinline__ Pos<double> make_pos<double>(uint32_t x, uint32_t y, uint32_t z, const uint32_t (&)[3]) {
+  return Pos<double>{x, y, z};
+}
+
 template <class R>
 struct WalkSmem {
   int32_t stack[kWarps][kStack];
-  Entry<R> e[kWarps][kList];
+  LEntry<R> e[kWarps][kList];
   R h[kWarps][kList];  // spline radius 2.8 eps of the entry (lattice units)
 };
 
@@ -148,14 +207,21 @@ __device__ __forceinline__ void inv_and_r(double r2, double& r, double& ir) {
   ir = 1.0 / r;
 }
 
-// squared lattice distance of entry E from particle (xi, yi, zi), from the
-// exact int32 minimum-image offsets
-template <class R>
-__device__ __forceinline__ R entry_r2(const Entry<R>& E, uint32_t xi, uint32_t yi, uint32_t zi, R& dx, R& dy,
-                                      R& dz) {
-  dx = (R)(int32_t)(E.x - xi);
-  dy = (R)(int32_t)(E.y - yi);
-  dz = (R)(int32_t)(E.z - zi);
+// squared lattice distance of entry E from the lane's particle P: FP32 from
+// the two offsets from the group centre, FP64 from the exact int32
+// minimum-image offsets
+__device__ __forceinline__ float entry_r2(const LEntry<float>& E, const Pos<float>& P, float& dx, float& dy,
+                                          float& dz) {
+  dx = E.x - P.x;
+  dy = E.y - P.y;
+  dz = E.z - P.z;
+  return dx * dx + dy * dy + dz * dz;
+}
+__device__ __forceinline__ double entry_r2(const LEntry<double>& E, const Pos<double>& P, double& dx, double& dy,
+                                           double& dz) {
+  dx = (double)(int32_t)(E.x - P.x);
+  dy = (double)(int32_t)(E.y - P.y);
+  dz = (double)(int32_t)(E.z - P.z);
   return dx * dx + dy * dy + dz * dz;
 }
 
@@ -185,10 +251,10 @@ __device__ __forceinline__ void pair_force(R dx, R dy, R dz, R r2, R m, R he, R 
 }
 
 template <class R>
-__device__ __forceinline__ void pair_in_range(const Entry<R>& E, R he, uint32_t xi, uint32_t yi, uint32_t zi, R hi,
+__device__ __forceinline__ void pair_in_range(const LEntry<R>& E, R he, const Pos<R>& P, R hi,
                                               const WalkConst<R>& C, R& ax, R& ay, R& az) {
   R dx, dy, dz;
-  const R r2 = entry_r2(E, xi, yi, zi, dx, dy, dz);
+  const R r2 = entry_r2(E, P, dx, dy, dz);
   pair_force(dx, dy, dz, r2, E.m, he, hi, C, ax, ay, az);
 }
 
@@ -198,19 +264,18 @@ __device__ __forceinline__ void pair_in_range(const Entry<R>& E, R he, uint32_t 
 // evaluates only the set bits, so the force arithmetic runs for in-range pairs
 // only and the warp iterates as often as its busiest lane has pairs in range.
 template <class R, bool kMasked>
-__device__ __forceinline__ void eval_list(const WalkSmem<R>& sm, int w, int len, int sub, int Sm, uint32_t xi,
-                                          uint32_t yi, uint32_t zi, R hi, const WalkConst<R>& C, R& ax, R& ay,
-                                          R& az, unsigned& nin) {
+__device__ __forceinline__ void eval_list(const WalkSmem<R>& sm, int w, int len, int sub, int Sm, const Pos<R>& P,
+                                          R hi, const WalkConst<R>& C, R& ax, R& ay, R& az, unsigned& nin) {
   if (!kMasked) {
     // most entries in range (a group cube small against r_cut): one pass,
     // the force arithmetic guarded by the range test
     int e = sub;
     for (; e + Sm < len; e += 2 * Sm) {  // two entries per iteration (independent chains)
-      const Entry<R> E0 = sm.e[w][e], E1 = sm.e[w][e + Sm];
+      const LEntry<R> E0 = sm.e[w][e], E1 = sm.e[w][e + Sm];
       const R h0 = sm.h[w][e], h1 = sm.h[w][e + Sm];
       R dx0, dy0, dz0, dx1, dy1, dz1;
-      const R r0 = entry_r2(E0, xi, yi, zi, dx0, dy0, dz0);
-      const R r1 = entry_r2(E1, xi, yi, zi, dx1, dy1, dz1);
+      const R r0 = entry_r2(E0, P, dx0, dy0, dz0);
+      const R r1 = entry_r2(E1, P, dx1, dy1, dz1);
       if (r0 < C.rcut2 && r0 > (R)0) {
         ++nin;
         pair_force(dx0, dy0, dz0, r0, E0.m, h0, hi, C, ax, ay, az);
@@ -221,9 +286,9 @@ __device__ __forceinline__ void eval_list(const WalkSmem<R>& sm, int w, int len,
       }
     }
     if (e < len) {
-      const Entry<R> E0 = sm.e[w][e];
+      const LEntry<R> E0 = sm.e[w][e];
       R dx, dy, dz;
-      const R r2 = entry_r2(E0, xi, yi, zi, dx, dy, dz);
+      const R r2 = entry_r2(E0, P, dx, dy, dz);
       if (r2 < C.rcut2 && r2 > (R)0) {
         ++nin;
         pair_force(dx, dy, dz, r2, E0.m, sm.h[w][e], hi, C, ax, ay, az);
@@ -236,11 +301,11 @@ __device__ __forceinline__ void eval_list(const WalkSmem<R>& sm, int w, int len,
   for (int kb = 0; kb < nkmax; kb += 32) {
     unsigned mask = 0;
     const int kend = nk - kb < 32 ? nk - kb : 32;
-    const Entry<R>* ep = &sm.e[w][sub + kb * Sm];
+    const LEntry<R>* ep = &sm.e[w][sub + kb * Sm];
 #pragma unroll 4
     for (int k = 0; k < kend; ++k) {
       R dx, dy, dz;
-      const R r2 = entry_r2(ep[k * Sm], xi, yi, zi, dx, dy, dz);
+      const R r2 = entry_r2(ep[k * Sm], P, dx, dy, dz);
       mask |= (r2 < C.rcut2 && r2 > (R)0) ? (1u << k) : 0u;
     }
     nin += __popc(mask);
@@ -249,7 +314,7 @@ __device__ __forceinline__ void eval_list(const WalkSmem<R>& sm, int w, int len,
         const int k = __ffs(mask) - 1;
         mask &= mask - 1u;
         const int e = sub + (kb + k) * Sm;
-        pair_in_range(sm.e[w][e], sm.h[w][e], xi, yi, zi, hi, C, ax, ay, az);
+        pair_in_range(sm.e[w][e], sm.h[w][e], P, hi, C, ax, ay, az);
       }
     }
   }
@@ -370,7 +435,7 @@ __global__ void __launch_bounds__(kWarps * 32, sizeof(R) == 4 ? 7 : 5) k_walk(
       const int m = lane % cnt, sub = lane / cnt;
       const int Sm = 32 / cnt + (m < 32 % cnt ? 1 : 0);
       const int i = gn.start + c0 + m;
-      const uint32_t xi = u[i], yi = u[cap + i], zi = u[2 * cap + i];
+      const Pos<R> P = make_pos<R>(u[i], u[cap + i], u[2 * cap + i], cg);
       const R hi = ph[i];
       R ax = 0, ay = 0, az = 0;
       if (C.tree) {
@@ -401,7 +466,7 @@ __global__ void __launch_bounds__(kWarps * 32, sizeof(R) == 4 ? 7 : 5) k_walk(
 #define DZS_WALK_FLUSH()                                                     \
   do {                                                                       \
     __syncwarp();                                                            \
-    eval_list<R, kMasked>(sm, w, len, sub, Sm, xi, yi, zi, hi, C, ax, ay, az, nin); \
+    eval_list<R, kMasked>(sm, w, len, sub, Sm, P, hi, C, ax, ay, az, nin);      \
     if (lane == 0) npairs += (unsigned)len * (unsigned)cnt;                  \
     glen += len;                                                             \
     len = 0;                                                                 \
@@ -477,12 +542,7 @@ __global__ void __launch_bounds__(kWarps * 32, sizeof(R) == 4 ? 7 : 5) k_walk(
           unsigned am = __ballot_sync(0xffffffffu, acc);
           if (acc) {
             int pos = len + __popc(am & lt);
-            Entry<R> E;
-            E.x = nd.comx;
-            E.y = nd.comy;
-            E.z = nd.comz;
-            E.m = C.gm0 * (R)nd.mass;
-            sm.e[w][pos] = E;
+            sm.e[w][pos] = make_entry(nd.comx, nd.comy, nd.comz, C.gm0 * (R)nd.mass, cg);
             sm.h[w][pos] = nh[ni];
           }
           len += __popc(am);
@@ -546,7 +606,7 @@ __global__ void __launch_bounds__(kWarps * 32, sizeof(R) == 4 ? 7 : 5) k_walk(
             const unsigned tm = __ballot_sync(0xffffffffu, take);
             if (take) {
               const int pos = len + __popc(tm & lt);
-              sm.e[w][pos] = E;
+              sm.e[w][pos] = make_entry(E.x, E.y, E.z, E.m, cg);
               sm.h[w][pos] = ph[j];
             }
             len += __popc(tm);
@@ -572,7 +632,7 @@ __global__ void __launch_bounds__(kWarps * 32, sizeof(R) == 4 ? 7 : 5) k_walk(
               const unsigned tm = __ballot_sync(0xffffffffu, take);
               if (take) {
                 const int pos = len + __popc(tm & lt);
-                sm.e[w][pos] = E;
+                sm.e[w][pos] = make_entry(E.x, E.y, E.z, E.m, cg);
                 sm.h[w][pos] = ph[j];
               }
               len += __popc(tm);
