@@ -61,6 +61,10 @@ def test_twin_runs(dzs, kw, bound_sky, bound_grid, bound_cl):
     assert sky <= bound_sky
     assert grid <= bound_grid
     assert np.median(cl) <= bound_cl
+    # the final-time P(k) at the two largest scales, where merged particles
+    # still carry the large-scale mass distribution (the paper avoids P(k) of
+    # the de-refined volume)
+    assert np.all(np.abs(pk[:2]) <= 2e-2), pk[:2]
 
 
 def lightcone_halos(dzs, kw, on, cadence=4, start=24):
