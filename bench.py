@@ -33,11 +33,12 @@ METRIC = "particle-steps/s DZS FP32 vs plain FP64 at stated force error; mocks/h
 UNIT = "particle-steps/s"
 # FP32 arithmetic of one in-range pair evaluation of the walk (Sec. 2.1 pair
 # force), counted from the code on the FMA pipe (FFMA = 2, FMUL/FADD = 1):
-# r^2 6 (FMUL + 2 FFMA + bias add), r = r^2 / sqrt 1, r^-3 2, polynomial
-# variable 2, split polynomial 22 (11 FFMA), exp2 argument 1, exp times Q 1,
-# force 2, accumulate 6; plus 2 SFU operations (rsqrt, exp2).  A listed pair
-# beyond r_cut costs only the r^2 test (6 flop) and is not algorithmic work.
-FMA_FLOP_PER_PAIR = 43
+# offsets from the group centre 3 (FADD), r^2 5 (FMUL + 2 FFMA), r = r^2 /
+# sqrt 1, r^-3 2, polynomial variable 2, split polynomial 22 (11 FFMA), exp2
+# argument 1, exp times Q 1, force 2, accumulate 6 (3 FFMA); plus 2 SFU
+# operations (rsqrt, exp2).  A listed pair beyond r_cut costs only the
+# offsets and the r^2 test (8 flop) and is not algorithmic work.
+FMA_FLOP_PER_PAIR = 45
 SFU_OPS_PER_PAIR = 2
 
 # algorithmic HBM bytes per step of the streaming stages (FP32 state: u 12 B,
