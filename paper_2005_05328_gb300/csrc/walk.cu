@@ -484,8 +484,10 @@ __global__ void __launch_bounds__(kWarps * 32, sizeof(R) == 4 ? 7 : 5) k_walk(
           __syncwarp();
           bool acc = false, leaf = false, inner = false;
           Node nd;
+          R nhi = 0;
           if (ni >= 0) {
             nd = nodes[ni];
+            nhi = nh[ni];  // the node's softening, loaded beside the node
             const int nlevel = (int)(nd.meta & 0xff);
             // 32-bit gaps (half extents: group hg <= 2^31, node hn <= 2^30 below
             // the root, so hg + hn < 2^32); squared sums in FP32 decide unless
@@ -543,7 +545,7 @@ __global__ void __launch_bounds__(kWarps * 32, sizeof(R) == 4 ? 7 : 5) k_walk(
           if (acc) {
             int pos = len + __popc(am & lt);
             sm.e[w][pos] = make_entry(nd.comx, nd.comy, nd.comz, C.gm0 * (R)nd.mass, cg);
-            sm.h[w][pos] = nh[ni];
+            sm.h[w][pos] = nhi;
           }
           len += __popc(am);
           // children of opened inner nodes onto the stack
@@ -597,17 +599,18 @@ __global__ void __launch_bounds__(kWarps * 32, sizeof(R) == 4 ? 7 : 5) k_walk(
             int sst = __shfl_sync(0xffffffffu, lstart, src);
             bool take = false;
             Entry<R> E;
-            int64_t j = 0;
+            R hj = 0;
             if (t < totl) {
-              j = (int64_t)sst + (t - (send - scnt));
+              const int64_t j = (int64_t)sst + (t - (send - scnt));
               E = pm[j];
+              hj = ph[j];  // loaded beside the entry, before the distance test
               take = near_group(E.x, E.y, E.z, cg, hg, C);
             }
             const unsigned tm = __ballot_sync(0xffffffffu, take);
             if (take) {
               const int pos = len + __popc(tm & lt);
               sm.e[w][pos] = make_entry(E.x, E.y, E.z, E.m, cg);
-              sm.h[w][pos] = ph[j];
+              sm.h[w][pos] = hj;
             }
             len += __popc(tm);
           }
@@ -623,17 +626,18 @@ __global__ void __launch_bounds__(kWarps * 32, sizeof(R) == 4 ? 7 : 5) k_walk(
               if (len + 32 > kList) DZS_WALK_FLUSH();
               bool take = false;
               Entry<R> E;
-              int64_t j = 0;
+              R hj = 0;
               if (q0 + lane < bc) {
-                j = (int64_t)bs + q0 + lane;
+                const int64_t j = (int64_t)bs + q0 + lane;
                 E = pm[j];
+                hj = ph[j];
                 take = near_group(E.x, E.y, E.z, cg, hg, C);
               }
               const unsigned tm = __ballot_sync(0xffffffffu, take);
               if (take) {
                 const int pos = len + __popc(tm & lt);
                 sm.e[w][pos] = make_entry(E.x, E.y, E.z, E.m, cg);
-                sm.h[w][pos] = ph[j];
+                sm.h[w][pos] = hj;
               }
               len += __popc(tm);
             }
