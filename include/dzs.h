@@ -340,6 +340,24 @@ typedef struct {
   dzs_params base;         /* everything but n1d, mesh, box, sigma8, seed (capacity ignored) */
 } dzs_serve_config;
 
+/* Batches (SURVEY's batching API for the batched and serving configurations;
+ * the paper has one simulation per run): a batch steps several contexts
+ * together.  dzs_batch_create keeps the n context pointers (it does not own
+ * the contexts; they must outlive the batch) and uses host_threads worker
+ * threads (0: min(8, hardware threads)).  dzs_batch_step enqueues up to
+ * nsteps steps on every context, `slice` steps at a time round-robin over each
+ * thread's share, so all streams get work early; it returns after enqueueing
+ * (like dzs_step), with steps_done[i] (nullable, n entries) the steps
+ * enqueued on context i, and the first failing status (the other contexts
+ * still step).  Each context's results are exactly those of stepping it
+ * alone.  dzs_batch_synchronize waits for every context's stream;
+ * dzs_batch_destroy frees the batch (NULL-safe), not the contexts. */
+typedef struct dzs_batch dzs_batch;
+DZS_API dzs_status dzs_batch_create(dzs_ctx* const* ctxs, int32_t n, int32_t host_threads, dzs_batch** out);
+DZS_API dzs_status dzs_batch_step(dzs_batch* b, int32_t nsteps, int32_t slice, int32_t* steps_done);
+DZS_API dzs_status dzs_batch_synchronize(dzs_batch* b);
+DZS_API dzs_status dzs_batch_destroy(dzs_batch* b);
+
 /* Serve n requests (any order of arrival_s) to completion on base.device;
  * out[i] belongs to req[i].  Returns DZS_OK, or the first failing status (the
  * other requests still run); a request that alone exceeds the budget gets

@@ -34,7 +34,8 @@ PK_SHOT = 1
 EXPORTED = ["dzs_params_default", "dzs_footprint_bytes", "dzs_create", "dzs_ics", "dzs_step",
             "dzs_run_stages", "dzs_lightcone_drain", "dzs_destroy", "dzs_get_count", "dzs_get_state",
             "dzs_set_state", "dzs_accel", "dzs_merge_only", "dzs_diagnostics", "dzs_get_tables",
-            "dzs_get_mesh", "dzs_get_counters", "dzs_get_walk_counters", "dzs_walk_lists", "dzs_measure_fp32_peaks", "dzs_debug_fail_alloc", "dzs_twin_displacement", "dzs_set_profiling", "dzs_get_profile",
+            "dzs_get_mesh", "dzs_get_counters", "dzs_get_walk_counters", "dzs_walk_lists", "dzs_measure_fp32_peaks", "dzs_debug_fail_alloc", "dzs_twin_displacement", "dzs_batch_create", "dzs_batch_step",
+            "dzs_batch_synchronize", "dzs_batch_destroy", "dzs_set_profiling", "dzs_get_profile",
             "dzs_morton_sort_noalloc", "dzs_checkpoint_bytes", "dzs_checkpoint", "dzs_restore",
             "dzs_step_until", "dzs_observe_enable", "dzs_observe_add_records", "dzs_skymap_get",
             "dzs_lcdensity_get", "dzs_skymap_alm", "dzs_power_spectrum", "dzs_serve", "dzs_fof", "dzs_last_error"]
@@ -124,6 +125,8 @@ def load(path: str = LIB_PATH):
         "dzs_walk_lists": [vp, vp, vp, vp, sz, C.POINTER(sz)],
         "dzs_measure_fp32_peaks": [i32, i32, C.POINTER(C.c_double), C.POINTER(C.c_double)],
         "dzs_debug_fail_alloc": [i32],
+        "dzs_batch_create": [vp, i32, i32, C.POINTER(vp)], "dzs_batch_step": [vp, i32, i32, vp],
+        "dzs_batch_synchronize": [vp], "dzs_batch_destroy": [vp],
         "dzs_twin_displacement": [vp, vp, vp, i32, vp, vp, C.POINTER(C.c_double)], "dzs_set_profiling": [vp, i32], "dzs_get_profile": [vp, vp, vp],
         "dzs_checkpoint_bytes": [vp, C.POINTER(sz)], "dzs_checkpoint": [vp, vp, sz, C.POINTER(sz)],
         "dzs_restore": [vp, vp, sz],
@@ -296,6 +299,43 @@ def dzs_measure_fp32_peaks(device=0, reps=5):
     if st != DZS_OK:
         raise RuntimeError("dzs_measure_fp32_peaks failed with status %d" % st)
     return f.value, s.value
+
+
+class Batch:
+    """Several contexts stepped together by host worker threads (dzs_batch_*);
+    the contexts stay the caller's."""
+
+    def __init__(self, contexts, host_threads=0):
+        self.contexts = list(contexts)
+        arr = (C.c_void_p * max(1, len(self.contexts)))(*[c.h for c in self.contexts])
+        h = C.c_void_p()
+        st = load().dzs_batch_create(arr, len(self.contexts), host_threads, C.byref(h))
+        if st != DZS_OK:
+            raise DzsError(st, "dzs_batch_create")
+        self.h = h
+
+    def step(self, nsteps, slice=8):
+        done = np.zeros(max(1, len(self.contexts)), np.int32)
+        st = load().dzs_batch_step(self.h, nsteps, slice, _ptr(done))
+        if st != DZS_OK:
+            raise DzsError(st, "dzs_batch_step")
+        return done[:len(self.contexts)]
+
+    def synchronize(self):
+        st = load().dzs_batch_synchronize(self.h)
+        if st != DZS_OK:
+            raise DzsError(st, "dzs_batch_synchronize")
+
+    def close(self):
+        if self.h:
+            load().dzs_batch_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def dzs_debug_fail_alloc(k):

@@ -18,6 +18,7 @@
 #include <cstring>
 #include <deque>
 #include <mutex>
+#include <new>
 #include <thread>
 #include <vector>
 
@@ -45,6 +46,89 @@ uint64_t fnv1a(const void* data, size_t len, uint64_t h) {
 }
 
 }  // namespace
+
+// ---- a batch of contexts stepped together: each host worker thread enqueues
+// the steps of its share of the contexts in slices, so every stream gets
+// work early and the launches of many small mocks are issued in parallel.
+// The contexts stay the caller's; results do not depend on the batch.
+struct dzs_batch {
+  std::vector<dzs_ctx*> ctx;
+  int threads = 1;
+};
+
+extern "C" dzs_status dzs_batch_create(dzs_ctx* const* ctxs, int32_t n, int32_t host_threads, dzs_batch** out) {
+  if (!out || n < 0 || (n > 0 && !ctxs) || host_threads < 0) return DZS_EINVAL;
+  *out = nullptr;
+  for (int32_t i = 0; i < n; ++i)
+    if (!ctxs[i]) return DZS_EINVAL;
+  dzs_batch* b = new (std::nothrow) dzs_batch();
+  if (!b) return DZS_ENOMEM;
+  b->ctx.assign(ctxs, ctxs + n);
+  int t = host_threads;
+  if (t == 0) {
+    const unsigned hw = std::thread::hardware_concurrency();
+    t = (int)std::min(8u, hw > 0 ? hw : 1u);
+  }
+  b->threads = std::max(1, std::min(t, std::max(1, (int)n)));
+  *out = b;
+  return DZS_OK;
+}
+
+extern "C" dzs_status dzs_batch_step(dzs_batch* b, int32_t nsteps, int32_t slice, int32_t* steps_done) {
+  if (!b || nsteps < 0 || slice < 1) return DZS_EINVAL;
+  const size_t n = b->ctx.size();
+  std::vector<int32_t> done(n, 0);
+  std::atomic<int> first_error{DZS_OK};
+  auto work = [&](int t) {
+    int dev = -1;
+    // round-robin slices over this thread's contexts (t, t + T, t + 2T, ...)
+    bool any = true;
+    while (any) {
+      any = false;
+      for (size_t i = (size_t)t; i < n; i += (size_t)b->threads) {
+        if (done[i] >= nsteps) continue;
+        dzs_ctx* c = b->ctx[i];
+        if (c->dev != dev) {
+          cudaSetDevice(c->dev);
+          dev = c->dev;
+        }
+        const int32_t k = std::min(slice, nsteps - done[i]);
+        int32_t got = 0;
+        const dzs_status st = dzs_step(c, k, &got);
+        done[i] += got;
+        if (st != DZS_OK) {
+          int expect = DZS_OK;
+          first_error.compare_exchange_strong(expect, (int)st);
+          done[i] = nsteps;  // this context stops here
+          continue;
+        }
+        if (got < k) done[i] = nsteps;  // reached a = 1
+        any = true;
+      }
+    }
+  };
+  std::vector<std::thread> th;
+  for (int t = 1; t < b->threads; ++t) th.emplace_back(work, t);
+  work(0);
+  for (auto& x : th) x.join();
+  if (steps_done)
+    for (size_t i = 0; i < n; ++i) steps_done[i] = std::min(done[i], nsteps);
+  return (dzs_status)first_error.load();
+}
+
+extern "C" dzs_status dzs_batch_synchronize(dzs_batch* b) {
+  if (!b) return DZS_EINVAL;
+  for (dzs_ctx* c : b->ctx) {
+    cudaSetDevice(c->dev);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return DZS_EDEVICE;
+  }
+  return DZS_OK;
+}
+
+extern "C" dzs_status dzs_batch_destroy(dzs_batch* b) {
+  delete b;
+  return DZS_OK;
+}
 
 extern "C" dzs_status dzs_serve(const dzs_serve_config* cfg, const dzs_request* req, size_t n,
                                 dzs_request_result* out, double* wall_s) {

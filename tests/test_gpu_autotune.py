@@ -60,3 +60,36 @@ def test_tuner_picks_and_caches(dzs, tmp_path, monkeypatch):
     assert autotune.tune_walk(32, 64, 64.0, dzs.FP32) == mode  # from the cache
     P = autotune.tuned_params(n1d=32, mesh=64, box=64.0, precision=dzs.FP32)
     assert P.walk_eval == mode and P.walk_group == 32 and P.leaf_bucket == 8
+
+
+def test_batch_api_results_equal_solo_runs(dzs):
+    """dzs_batch_*: six mocks of four sizes stepped together by worker threads
+    (each on its own stream) end bit-identical to the same mocks stepped alone"""
+    import torch
+    shapes = [(16, 32, 5), (32, 64, 6), (24, 48, 7), (16, 32, 8), (32, 64, 9), (48, 96, 10)]
+    solo = []
+    for n1, m, seed in shapes:
+        with dzs.Context(n1d=n1, mesh=m, box=2.0 * n1, seed=seed, precision=dzs.FP32) as ctx:
+            ctx.ics()
+            ctx.step(40)
+            solo.append((ctx.state(), ctx.drain()))
+    streams = [torch.cuda.Stream() for _ in shapes]
+    ctxs = [dzs.Context(n1d=n1, mesh=m, box=2.0 * n1, seed=seed, precision=dzs.FP32, stream=s.cuda_stream)
+            for (n1, m, seed), s in zip(shapes, streams)]
+    try:
+        for c in ctxs:
+            c.ics()
+        with dzs.Batch(ctxs, host_threads=3) as b:
+            done = b.step(25, slice=4)
+            assert list(done) == [25] * len(ctxs)
+            done = b.step(15, slice=7)
+            assert list(done) == [15] * len(ctxs)
+            b.synchronize()
+        for c, (st, rec) in zip(ctxs, solo):
+            s2 = c.state()
+            for key in st:
+                assert np.array_equal(s2[key], st[key]), key
+            assert c.drain().tobytes() == rec.tobytes()
+    finally:
+        for c in ctxs:
+            c.close()
