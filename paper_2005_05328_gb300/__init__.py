@@ -207,8 +207,11 @@ def dzs_get_count(h):
     return n.value, st.value
 
 
-def dzs_lightcone_drain(h, cap: int = 1 << 22):
-    buf = np.zeros(cap, RECORD_DTYPE)
+def dzs_lightcone_drain(h, cap: int = 1 << 22, buf=None):
+    """records drained (at most cap), copied out of `buf` (reused when given
+    and large enough)"""
+    if buf is None or len(buf) < cap:
+        buf = np.empty(cap, RECORD_DTYPE)
     n = C.c_size_t(0)
     _check(load().dzs_lightcone_drain(h, _ptr(buf), cap, C.byref(n)), h)
     return buf[:n.value].copy()
@@ -501,7 +504,10 @@ class Context:
     def step(self, n=1): return dzs_step(self.h, n)
     def run_stages(self, mask): dzs_run_stages(self.h, mask)
     def count(self): return dzs_get_count(self.h)
-    def drain(self, cap=1 << 22): return dzs_lightcone_drain(self.h, cap)
+    def drain(self, cap=1 << 22):
+        if getattr(self, "_drain_buf", None) is None or len(self._drain_buf) < cap:
+            self._drain_buf = np.empty(cap, RECORD_DTYPE)
+        return dzs_lightcone_drain(self.h, cap, self._drain_buf)
     def state(self): return dzs_get_state(self.h)
     def set_state(self, st, step, with_g=True): dzs_set_state(self.h, st, step, with_g)
     def accel(self, parts=ACC_ALL): return dzs_accel(self.h, parts)

@@ -139,7 +139,18 @@ __global__ void k_diag_partial(const int32_t* __restrict__ d_n, int64_t cap, con
     }
   }
   __shared__ double sh[3][kThreads];
+  __shared__ unsigned long long ish[4][kThreads / 32];
   for (int ax = 0; ax < 3; ++ax) sh[ax][threadIdx.x] = s[ax];
+  // integer sums: warp shuffles, then one atomic per block and sum (exact in
+  // any order; an atomic per thread serialised on four addresses)
+  for (int o = 16; o > 0; o >>= 1) {
+    ks += __shfl_down_sync(0xffffffffu, ks, o);
+    for (int ax = 0; ax < 3; ++ax) us[ax] += __shfl_down_sync(0xffffffffu, us[ax], o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    ish[0][threadIdx.x >> 5] = ks;
+    for (int ax = 0; ax < 3; ++ax) ish[1 + ax][threadIdx.x >> 5] = us[ax];
+  }
   __syncthreads();
   for (int w = blockDim.x / 2; w > 0; w >>= 1) {
     if ((int)threadIdx.x < w)
@@ -148,22 +159,31 @@ __global__ void k_diag_partial(const int32_t* __restrict__ d_n, int64_t cap, con
   }
   if (threadIdx.x == 0)
     for (int ax = 0; ax < 3; ++ax) part[ax * kDiagBlocks + blockIdx.x] = sh[ax][0];
-  atomicAdd(&isum[0], ks);
-  for (int ax = 0; ax < 3; ++ax) atomicAdd(&isum[1 + ax], us[ax]);
+  if (threadIdx.x < 4) {
+    unsigned long long t = 0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += ish[threadIdx.x][q];
+    atomicAdd(&isum[threadIdx.x], t);
+  }
 }
 
+// one warp per axis: lane-strided sums of the block partials, then a fixed
+// shuffle tree (the same order every call)
 __global__ void k_diag_final(const int32_t* __restrict__ d_n, const double* __restrict__ part,
                              const unsigned long long* __restrict__ isum, double* __restrict__ out,
                              double scale) {
-  if (threadIdx.x != 0) return;
-  out[0] = (double)isum[0];
-  for (int ax = 0; ax < 3; ++ax) {
-    double s = 0;
-    for (int b = 0; b < kDiagBlocks; ++b) s += part[ax * kDiagBlocks + b];
+  const int ax = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (ax >= 3) return;
+  double s = 0;
+  for (int b = lane; b < kDiagBlocks; b += 32) s += part[ax * kDiagBlocks + b];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0) {
     out[1 + ax] = s;
     out[4 + ax] = (double)isum[1 + ax] * scale;
+    if (ax == 0) {
+      out[0] = (double)isum[0];
+      out[7] = (double)*d_n;
+    }
   }
-  out[7] = (double)*d_n;
 }
 
 template <class S, class D>
@@ -240,7 +260,7 @@ void launch_diagnostics(dzs_ctx* c) {
   else
     k_diag_partial<float><<<kDiagBlocks, kThreads, 0, c->stream>>>(c->B.n, c->cap, c->B.u,
                                                                    (const float*)c->B.p, c->B.k, part, isum);
-  k_diag_final<<<1, 32, 0, c->stream>>>(c->B.n, part, isum, c->B.diag, c->scale);
+  k_diag_final<<<1, 96, 0, c->stream>>>(c->B.n, part, isum, c->B.diag, c->scale);
 }
 
 void launch_to_double(dzs_ctx* c, const void* src, int64_t count, double* dst) {
