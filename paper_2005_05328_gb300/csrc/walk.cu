@@ -549,16 +549,22 @@ __global__ void __launch_bounds__(kWarps * 32, sizeof(R) == 4 ? 7 : 5) k_walk(
           }
           len += __popc(am);
           // children of opened inner nodes onto the stack
+          // one scan for both counts: children (<= 8 per lane, total < 2^16) in
+          // the low half, leaf particles (<= B <= 14 per lane) in the high half
           int nch = inner ? (int)((nd.meta >> 8) & 0xff) : 0;
-          int ex = warp_incl_scan<R>(nch, lane);
-          int tot = __shfl_sync(0xffffffffu, ex, 31);
-          ex -= nch;
+          int lc = (leaf && nd.count <= C.B) ? nd.count : 0;
+          const int both = warp_incl_scan<R>(nch | (lc << 16), lane);
+          int ex = (both & 0xffff) - nch;
+          int tot = __shfl_sync(0xffffffffu, both & 0xffff, 31);
+          const int incl = both >> 16;
           if (top + tot > kStack) {
             if (lane == 0) atomicOr(err, kErrStack);
             nch = 0;
             tot = 0;
           }
-          for (int q = 0; q < nch; ++q) sm.stack[w][top + ex + q] = nd.child + q;
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            if (q < nch) sm.stack[w][top + ex + q] = nd.child + q;
           top += tot;
           maxtop = top > maxtop ? top : maxtop;
           // particles of opened small leaves, copied cooperatively (item t of
@@ -568,8 +574,6 @@ __global__ void __launch_bounds__(kWarps * 32, sizeof(R) == 4 ? 7 : 5) k_walk(
           // leaves whose particles do not fit in the list this round go back
           // on the stack (the inclusive ends grow with the lane, so the ones
           // that fit are a prefix); after the next evaluation they fit
-          int lc = (leaf && nd.count <= C.B) ? nd.count : 0;
-          int incl = warp_incl_scan<R>(lc, lane);
           const int room = kList - len;
           const bool defer = lc > 0 && incl > room;
           const unsigned dm = __ballot_sync(0xffffffffu, defer);
@@ -585,7 +589,8 @@ __global__ void __launch_bounds__(kWarps * 32, sizeof(R) == 4 ? 7 : 5) k_walk(
           // items of the leaves that stay: the largest inclusive end within
           // the room (lanes past a deferred leaf carry its items in incl)
           const int totl = (int)__reduce_max_sync(0xffffffffu, (unsigned)(incl <= room ? incl : 0));
-          int lstart = leaf ? nd.start : 0;
+          // item t of the owner lane is particle jbase_owner + t
+          const int jbase = leaf ? nd.start - (incl - lc) : 0;
           for (int b0 = 0; b0 < totl; b0 += 32) {
             int t = b0 + lane;
             int src = 0;
@@ -594,14 +599,12 @@ __global__ void __launch_bounds__(kWarps * 32, sizeof(R) == 4 ? 7 : 5) k_walk(
               int v = __shfl_sync(0xffffffffu, incl, src + step - 1);
               if (v <= t) src += step;
             }
-            int send = __shfl_sync(0xffffffffu, incl, src);
-            int scnt = __shfl_sync(0xffffffffu, lc, src);
-            int sst = __shfl_sync(0xffffffffu, lstart, src);
+            const int jb = __shfl_sync(0xffffffffu, jbase, src);
             bool take = false;
             Entry<R> E;
             R hj = 0;
             if (t < totl) {
-              const int64_t j = (int64_t)sst + (t - (send - scnt));
+              const int64_t j = (int64_t)jb + t;
               E = pm[j];
               hj = ph[j];  // loaded beside the entry, before the distance test
               take = near_group(E.x, E.y, E.z, cg, hg, C);
