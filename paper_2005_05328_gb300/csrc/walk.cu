@@ -493,27 +493,24 @@ __global__ void __launch_bounds__(kWarps * 32, sizeof(R) == 4 ? 7 : 5) k_walk(
             // the root, so hg + hn < 2^32); squared sums in FP32 decide unless
             // they fall within 2^-20 of the exact integer threshold, where the
             // uint64 sum decides -- the same decision as the integer rule
-            bool touch = true;
             uint32_t gp[3], dmv[3];
             float d2f = 0.f, c2f = 0.f;
             const uint32_t cn[3] = {nd.cx, nd.cy, nd.cz};
             const uint32_t cm[3] = {nd.comx, nd.comy, nd.comz};
-            const uint32_t hn = nlevel == 0 ? 0u : (1u << (31 - nlevel));
+            // gap = max(|dc|, h) - h; the root touches everything (h = max)
+            const uint32_t h = nlevel == 0 ? 0xffffffffu : hg + (1u << (31 - nlevel));
 #pragma unroll
             for (int a3 = 0; a3 < 3; ++a3) {
-              int32_t ds = (int32_t)(cn[a3] - cg[a3]);
-              uint32_t dc = ds < 0 ? 0u - (uint32_t)ds : (uint32_t)ds;
-              uint32_t h = hg + hn;
-              uint32_t gap = (nlevel > 0 && dc > h) ? dc - h : 0u;
-              touch = touch && gap == 0u;
+              const uint32_t dc = (uint32_t)abs((int32_t)(cn[a3] - cg[a3]));
+              const uint32_t gap = max(dc, h) - h;
               gp[a3] = gap;
               d2f = fmaf((float)gap, (float)gap, d2f);
-              int32_t ms = (int32_t)(cm[a3] - cg[a3]);
-              uint32_t mc = ms < 0 ? 0u - (uint32_t)ms : (uint32_t)ms;
-              uint32_t dm = mc > hg ? mc - hg : 0u;
+              const uint32_t mc = (uint32_t)abs((int32_t)(cm[a3] - cg[a3]));
+              const uint32_t dm = max(mc, hg) - hg;
               dmv[a3] = dm;
               c2f = fmaf((float)dm, (float)dm, c2f);
             }
+            const bool touch = (gp[0] | gp[1] | gp[2]) == 0u;
             bool keep = touch;
             if (!touch) {
               if (d2f <= C.skip_lo)
