@@ -416,8 +416,11 @@ DZS_API dzs_status dzs_get_counters(dzs_ctx* c, uint64_t out[9]);
  * dzs_get_counters' [2]: [0] listed pairs (interaction-list entries x group
  * particles, the same count as dzs_get_counters [2]), [1] pairs evaluated in
  * range (0 < r < r_cut: the pairs that carry force), [2] node tests, [3]
- * traversal rounds.  Synchronises the context stream. */
-DZS_API dzs_status dzs_get_walk_counters(dzs_ctx* c, uint64_t out[4]);
+ * traversal rounds, [4] group walks started from the window of deep frontier
+ * cells around the group, [5] group walks that fell back to the shallow
+ * frontier (a node between the two frontier depths might have been accepted).
+ * Synchronises the context stream. */
+DZS_API dzs_status dzs_get_walk_counters(dzs_ctx* c, uint64_t out[6]);
 
 /* Interaction lists of the last tree walk, per walk group (Eq. 1 applied per
  * group: a node with <= walk_group particles whose parent holds more, or a

@@ -289,8 +289,9 @@ def dzs_get_counters(h):
 
 
 def dzs_get_walk_counters(h):
-    """[listed pairs, in-range pairs, node tests, traversal rounds]"""
-    out = np.zeros(4, np.uint64)
+    """[listed pairs, in-range pairs, node tests, traversal rounds, group walks
+    started from the deep frontier window, fallbacks to the shallow frontier]"""
+    out = np.zeros(6, np.uint64)
     _check(load().dzs_get_walk_counters(h, _ptr(out)), h)
     return out
 

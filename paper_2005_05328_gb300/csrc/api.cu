@@ -709,6 +709,7 @@ dzs_status dzs_set_state(dzs_ctx* c, const uint32_t* u, const double* p, const d
   CK(cudaMemset(c->B.err, 0, 16));
   CK(cudaMemset(c->B.counters + 4, 0, 4 * sizeof(uint64_t)));  // pairs and stack depth (4, 7)
   CK(cudaMemset(c->B.counters + 12, 0, 2 * sizeof(uint64_t)));  // node tests, rounds
+  CK(cudaMemset(c->B.counters + 20, 0, 2 * sizeof(uint64_t)));  // window starts, fallbacks
   c->step = step;
   c->have_state = true;
   c->g_aligned = true;
@@ -1122,6 +1123,7 @@ dzs_status dzs_set_profiling(dzs_ctx* c, int32_t enable) {
   }
   CK(cudaMemsetAsync(c->B.counters + 4, 0, 4 * sizeof(uint64_t), c->stream));
   CK(cudaMemsetAsync(c->B.counters + 12, 0, 2 * sizeof(uint64_t), c->stream));
+  CK(cudaMemsetAsync(c->B.counters + 20, 0, 2 * sizeof(uint64_t), c->stream));
   c->prof_on = enable != 0;
   return DZS_OK;
 }
@@ -1216,17 +1218,19 @@ dzs_status dzs_twin_displacement(dzs_ctx* a, dzs_ctx* b, const double* edges, in
   return st;
 }
 
-dzs_status dzs_get_walk_counters(dzs_ctx* c, uint64_t out[4]) {
+dzs_status dzs_get_walk_counters(dzs_ctx* c, uint64_t out[6]) {
   dzs_status s = guard(c);
   if (s) return s;
   if (!out) return fail(c, DZS_EINVAL, "out is NULL");
   CK(cudaStreamSynchronize(c->stream));
-  uint64_t ctr[16];
+  uint64_t ctr[22];
   CK(cudaMemcpy(ctr, c->B.counters, sizeof ctr, cudaMemcpyDeviceToHost));
   out[0] = ctr[4];
   out[1] = ctr[5];
   out[2] = ctr[12];
   out[3] = ctr[13];
+  out[4] = ctr[20];
+  out[5] = ctr[21];
   return DZS_OK;
 }
 

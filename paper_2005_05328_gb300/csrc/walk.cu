@@ -161,6 +161,10 @@ struct WalkConst {
   int poly;  // FP32: use the fitted split polynomial (x_max <= 2.5)
   int front;                  // frontier depth f (0: start at the root)
   const int32_t* ftab;        // [2^f]^3 row-major: node of each depth-f cell, -1 if empty
+  int frontF;                 // window frontier depth F > f (0: none)
+  uint32_t rcx;               // largest integer gap with gap^2 <= skip_d2
+  const int32_t* ftabF;       // [2^F]^3: node of each depth-F cell (or the leaf above it), -1 if empty
+  const uint8_t* fspanF;      // its F - depth, bit 7: an ancestor at depths [f, F) may accept
 };
 
 __device__ __forceinline__ uint64_t exact_d2(const uint32_t (&v)[3]) {
@@ -225,6 +229,13 @@ __device__ __forceinline__ double entry_r2(const LEntry<double>& E, const Pos<do
   return dx * dx + dy * dy + dz * dz;
 }
 
+// 0 < r2 < r_cut^2 (the self pair has r2 = 0): on the FP32 bit patterns,
+// which order like the values for r2 >= 0, one unsigned compare
+__device__ __forceinline__ bool in_range(float r2, float rcut2) {
+  return __float_as_uint(r2) - 1u < __float_as_uint(rcut2) - 1u;
+}
+__device__ __forceinline__ bool in_range(double r2, double rcut2) { return r2 < rcut2 && r2 > 0.0; }
+
 // force of one entry at offset (dx, dy, dz), 0 < r^2 < r_cut^2 (the caller
 // has tested the range)
 template <class R>
@@ -276,11 +287,11 @@ __device__ __forceinline__ void eval_list(const WalkSmem<R>& sm, int w, int len,
       R dx0, dy0, dz0, dx1, dy1, dz1;
       const R r0 = entry_r2(E0, P, dx0, dy0, dz0);
       const R r1 = entry_r2(E1, P, dx1, dy1, dz1);
-      if (r0 < C.rcut2 && r0 > (R)0) {
+      if (in_range(r0, C.rcut2)) {
         ++nin;
         pair_force(dx0, dy0, dz0, r0, E0.m, h0, hi, C, ax, ay, az);
       }
-      if (r1 < C.rcut2 && r1 > (R)0) {
+      if (in_range(r1, C.rcut2)) {
         ++nin;
         pair_force(dx1, dy1, dz1, r1, E1.m, h1, hi, C, ax, ay, az);
       }
@@ -289,7 +300,7 @@ __device__ __forceinline__ void eval_list(const WalkSmem<R>& sm, int w, int len,
       const LEntry<R> E0 = sm.e[w][e];
       R dx, dy, dz;
       const R r2 = entry_r2(E0, P, dx, dy, dz);
-      if (r2 < C.rcut2 && r2 > (R)0) {
+      if (in_range(r2, C.rcut2)) {
         ++nin;
         pair_force(dx, dy, dz, r2, E0.m, sm.h[w][e], hi, C, ax, ay, az);
       }
@@ -306,7 +317,7 @@ __device__ __forceinline__ void eval_list(const WalkSmem<R>& sm, int w, int len,
     for (int k = 0; k < kend; ++k) {
       R dx, dy, dz;
       const R r2 = entry_r2(ep[k * Sm], P, dx, dy, dz);
-      mask |= (r2 < C.rcut2 && r2 > (R)0) ? (1u << k) : 0u;
+      mask |= in_range(r2, C.rcut2) ? (1u << k) : 0u;
     }
     nin += __popc(mask);
     while (__any_sync(0xffffffffu, mask != 0u)) {
@@ -330,9 +341,8 @@ __device__ __forceinline__ bool near_group(uint32_t px, uint32_t py, uint32_t pz
   float d2f = 0.f;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const int32_t ms = (int32_t)(pp[a] - cg[a]);
-    const uint32_t mc = ms < 0 ? 0u - (uint32_t)ms : (uint32_t)ms;
-    const uint32_t dm = mc > hg ? mc - hg : 0u;
+    const uint32_t mc = (uint32_t)abs((int32_t)(pp[a] - cg[a]));
+    const uint32_t dm = max(mc, hg) - hg;
     dv[a] = dm;
     d2f = fmaf((float)dm, (float)dm, d2f);
   }
@@ -401,6 +411,59 @@ __global__ void k_front_fill(const int32_t* __restrict__ lvl, const Node* __rest
   }
 }
 
+// window frontier table at depth F > f: every node of depth F, and every leaf
+// above it, writes its index into the depth-F cells it covers, with F - depth
+// and a flag for an ancestor at depths [f, F) that some group might accept.
+// An ancestor a is "always opened" when every group cube within r_cut of its
+// cube opens it: the COM distance to any such group cube is at most
+// sqrt(skip_d2) + (distance from the COM to the farthest corner of a's cube),
+// and that passes the open test of a's depth.  Below always-opened ancestors
+// the per-group walk reaches exactly the depth-F nodes within r_cut.
+struct OpenD2 {
+  uint64_t v[kMaxLevel + 1];
+};
+__global__ void k_front_fill_F(const int32_t* __restrict__ lvl, const Node* __restrict__ nodes,
+                               const int32_t* __restrict__ parent, int f, int F, double skip_r, OpenD2 open_d2,
+                               int32_t* __restrict__ ftab, uint8_t* __restrict__ fspan) {
+  int64_t nF = 0;
+  for (int j = 0; j <= F; ++j) nF += lvl[j];
+  const int D = 1 << F;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nF; t += (int64_t)gridDim.x * blockDim.x) {
+    const Node nd = nodes[t];
+    const int j = (int)(nd.meta & 0xff);
+    if (j < F && nd.child >= 0) continue;  // internal above F: its depth-F descendants write
+    bool may_accept = false;
+    for (int32_t a = parent[t]; a >= 0; a = parent[a]) {
+      const Node an = nodes[a];
+      const int ja = (int)(an.meta & 0xff);
+      if (ja < f) break;  // above f no node is ever accepted
+      const uint64_t od = open_d2.v[ja];
+      if (od == ~0ull) continue;  // opens at every distance
+      const double ha = (double)(1u << (31 - ja));
+      double far2 = 0.0;
+      const uint32_t cm[3] = {an.comx, an.comy, an.comz}, cn[3] = {an.cx, an.cy, an.cz};
+      for (int q = 0; q < 3; ++q) {
+        const double d = fabs((double)(int32_t)(cm[q] - cn[q])) + ha;
+        far2 += d * d;
+      }
+      const double bound = skip_r + sqrt(far2);
+      if (!(bound * bound * (1.0 + 1e-9) + 4.0 <= (double)od)) may_accept = true;
+    }
+    const int span = 1 << (F - j);
+    const uint32_t h = j == 0 ? 0x80000000u : (1u << (31 - j));
+    const int x0 = (int)((nd.cx - h) >> (32 - F)), y0 = (int)((nd.cy - h) >> (32 - F)),
+              z0 = (int)((nd.cz - h) >> (32 - F));
+    const uint8_t sp = (uint8_t)((F - j) | (may_accept ? 0x80 : 0));
+    for (int a = 0; a < span; ++a)
+      for (int b = 0; b < span; ++b)
+        for (int c = 0; c < span; ++c) {
+          const int64_t cell = ((int64_t)(x0 + a) * D + (y0 + b)) * D + (z0 + c);
+          ftab[cell] = (int32_t)t;
+          fspan[cell] = sp;
+        }
+  }
+}
+
 // kMasked: evaluate lists with the range-masked pass (pays off when many
 // listed entries lie beyond r_cut of a given particle: groups not small
 // against r_cut), else with one range-guarded pass
@@ -419,6 +482,7 @@ __global__ void __launch_bounds__(kWarps * 32, sizeof(R) == 4 ? 7 : 5) k_walk(
   unsigned nin = 0;               // pairs in range (0 < r < r_cut) evaluated by this lane
   int maxtop = 0;  // deepest stack use of this warp (diagnostic)
   unsigned ntests = 0, nrounds = 0;  // node tests and traversal rounds of this warp (diagnostic)
+  unsigned nwin = 0, nfall = 0;      // group passes started from the depth-F window, and fallbacks
   for (;;) {
     int gi = 0;
     if (lane == 0) gi = (int)atomicAdd(next, 1u);
@@ -440,7 +504,56 @@ __global__ void __launch_bounds__(kWarps * 32, sizeof(R) == 4 ? 7 : 5) k_walk(
       R ax = 0, ay = 0, az = 0;
       if (C.tree) {
         int top = 0, len = 0, glen = 0;
-        if (C.front > 0 && glevel >= C.front) {
+        bool started = false;
+        if (C.frontF > 0 && glevel >= C.frontF - 1) {
+          // the depth-F nodes (or leaves above F) of the cells within r_cut of
+          // the group cube along every axis, each once (pushed from the first
+          // window cell it covers), when no ancestor of theirs at depths
+          // [f, F) can be accepted: the walk from f would open or skip those
+          // ancestors, so the same nodes get tested
+          const int F = C.frontF, shF = 32 - F;
+          const uint32_t Dm = (1u << F) - 1u;
+          uint32_t lo[3], na[3];
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            lo[a] = (cg[a] - hg - C.rcx - 1u) >> shF;
+            const uint32_t hi = (cg[a] + hg + C.rcx) >> shF;
+            na[a] = ((hi - lo[a]) & Dm) + 1u;
+          }
+          if (na[0] <= 6u && na[1] <= 6u && na[2] <= 6u) {
+            const int nyz = (int)(na[1] * na[2]), total = (int)na[0] * nyz;
+            bool bad = false;
+            for (int b = 0; b < total; b += 32) {
+              const int q = b + lane;
+              bool push = false;
+              int ni = -1;
+              if (q < total) {
+                const uint32_t qx = (uint32_t)(q / nyz), qr = (uint32_t)(q - (int)qx * nyz);
+                const uint32_t qy = qr / na[2], qz = qr - qy * na[2];
+                const uint32_t x = (lo[0] + qx) & Dm, y = (lo[1] + qy) & Dm, z = (lo[2] + qz) & Dm;
+                const int64_t cell = ((int64_t)x * (Dm + 1) + y) * (Dm + 1) + z;
+                ni = C.ftabF[cell];
+                if (ni >= 0) {
+                  const uint32_t sp = C.fspanF[cell];
+                  bad = bad || (sp & 0x80u) != 0u;
+                  const uint32_t e = sp & 0x7fu, sm1 = (1u << e) - 1u;
+                  const bool whole = (int)e == F;  // one leaf covers the box: first window cell only
+                  push = (qx == 0u || (!whole && (x & sm1) == 0u)) && (qy == 0u || (!whole && (y & sm1) == 0u)) &&
+                         (qz == 0u || (!whole && (z & sm1) == 0u));
+                }
+              }
+              const unsigned pmk = __ballot_sync(0xffffffffu, push);
+              if (push) sm.stack[w][top + __popc(pmk & lt)] = ni;
+              top += __popc(pmk);
+            }
+            started = !__any_sync(0xffffffffu, bad);
+            if (!started) top = 0;
+            nwin += started ? 1u : 0u;
+            nfall += started ? 0u : 1u;
+          }
+        }
+        if (started) {
+        } else if (C.front > 0 && glevel >= C.front) {
           // the nodes of the 27 cells around the group's depth-f cell, each once
           const int f = C.front, D = 1 << f;
           int ni = -1;
@@ -681,6 +794,8 @@ __global__ void __launch_bounds__(kWarps * 32, sizeof(R) == 4 ? 7 : 5) k_walk(
   if (lane == 0) atomicMax(pairs + 3, (unsigned long long)maxtop);
   if (lane == 0) atomicAdd(pairs + 8, (unsigned long long)ntests);
   if (lane == 0) atomicAdd(pairs + 9, (unsigned long long)nrounds);
+  if (lane == 0 && nwin) atomicAdd(pairs + 16, (unsigned long long)nwin);
+  if (lane == 0 && nfall) atomicAdd(pairs + 17, (unsigned long long)nfall);
 }
 
 template <class R>
@@ -714,6 +829,10 @@ void walk_impl(dzs_ctx* c, bool tree, bool close_kick, int step) {
   // its cells are wider than r_cut (cells beyond the 27 neighbours are skipped)
   C.front = 0;
   C.ftab = c->B.iscan;  // scratch: the tree's tile counts are no longer needed
+  C.frontF = 0;
+  C.rcx = 0;
+  C.ftabF = nullptr;
+  C.fspanF = nullptr;
   const int64_t ftab_cap = 2 * c->cap + 64;
   for (int f = 1; f <= 7 && ((int64_t)1 << (3 * f)) <= ftab_cap; ++f) {
     const double lf = std::ldexp(1.0, 32 - f), lp = std::ldexp(1.0, 33 - f);
@@ -723,6 +842,30 @@ void walk_impl(dzs_ctx* c, bool tree, bool close_kick, int step) {
     const bool wide = lf * lf > (double)C.skip_d2 * (1.0 + 1e-9);
     if (!(never && wide)) break;
     C.front = f;
+  }
+  // window frontier depth F (f + 2, else f + 1): the window of a group at
+  // depth >= F - 1 spans at most 6 depth-F cells per axis and at most half
+  // the box, and both tables fit in the scratch
+  if (C.front > 0 && tree) {
+    uint64_t r = (uint64_t)std::sqrt((double)C.skip_d2);
+    while (r * r > C.skip_d2) --r;
+    while ((r + 1) * (r + 1) <= C.skip_d2) ++r;
+    const int64_t cells_f = (int64_t)1 << (3 * C.front);
+    for (int F = C.front + 2; F > C.front; --F) {
+      if (F > kMaxLevel || r >= (1ull << 30)) continue;
+      const int64_t cells = (int64_t)1 << (3 * F);
+      const int64_t off = (cells_f + 3) & ~(int64_t)3;
+      if (off + cells + (cells + 3) / 4 > ftab_cap) continue;
+      const uint64_t sF = 1ull << (32 - F);
+      const uint64_t npts = 2 * sF + 2 * r + 2;  // lattice points of the widest window (inclusive)
+      const uint64_t nmax = (npts - 1) / sF + 2;
+      if (nmax > 6 || 2 * nmax > (1ull << F)) continue;
+      C.frontF = F;
+      C.rcx = (uint32_t)r;
+      C.ftabF = c->B.iscan + off;
+      C.fspanF = (const uint8_t*)(c->B.iscan + off + cells);
+      break;
+    }
   }
   Entry<R>* pm = (Entry<R>*)c->B.wpm;
   R* ph = (R*)c->B.wph;
@@ -736,6 +879,17 @@ void walk_impl(dzs_ctx* c, bool tree, bool close_kick, int step) {
     cudaMemsetAsync(c->B.iscan, 0xff, sizeof(int32_t) * cells, c->stream);
     k_front_fill<<<grid_for(cells, kThreads, 4), kThreads, 0, c->stream>>>(c->B.lvl_count, c->B.nodes, C.front,
                                                                                c->B.iscan);
+    if (C.frontF > 0) {
+      const int64_t cellsF = (int64_t)1 << (3 * C.frontF);
+      c->launches += 1;
+      cudaMemsetAsync((void*)C.ftabF, 0xff, sizeof(int32_t) * cellsF, c->stream);
+      cudaMemsetAsync((void*)C.fspanF, 0, (size_t)cellsF, c->stream);
+      OpenD2 od;
+      for (int l = 0; l <= kMaxLevel; ++l) od.v[l] = C.open_d2[l];
+      k_front_fill_F<<<grid_for(cellsF, kThreads, 4), kThreads, 0, c->stream>>>(
+          c->B.lvl_count, c->B.nodes, c->B.parent, C.front, C.frontF, std::sqrt((double)C.skip_d2), od,
+          (int32_t*)C.ftabF, (uint8_t*)C.fspanF);
+    }
   }
   // automatic: the range-masked evaluation when the walk groups of a uniform
   // particle set (leaves of ~B particles, side ~2 spacings) are at least
