@@ -23,6 +23,16 @@
 // decision equals a plain IEEE evaluation bit for bit.  a_min^2 is reduced
 // on the device just before the mark pass from the accelerations the state
 // carries (the previous step's forces) and the crossing flags of this step.
+//
+// Steps where little can merge cost little: a level whose T_j is beyond the
+// largest possible COM distance (the box corner) is never tested, and with
+// the geometric criterion (members must lie beyond R_lat + b_lat) a first
+// mark pass sums the few particles of each candidate cell directly; only when
+// some candidate cell holds more than kDirect particles are the prefix sums
+// built and those candidates marked again from them (same decisions: the sums
+// are exact either way).  The compaction writes only from the first particle
+// that changes, into the spare arrays, and copies that tail back: a step that
+// merges nothing writes nothing.
 #include <cmath>
 
 #include "common.cuh"
@@ -31,11 +41,14 @@ namespace dzs {
 namespace {
 
 constexpr int kChunk = 1024;
+constexpr int kDirect = 64;              // largest cell the first mark pass sums directly
+constexpr int32_t kDeferred = INT32_MIN;  // mend of a candidate left to the prefix pass
 
 struct MergeParams {
   uint64_t thr[kMaxLevel + 1];  // T_j (UINT64_MAX: level never merges)
   uint64_t rb2;                 // (R_lat + b_lat)^2: members must lie beyond
   int jmin;
+  int jstart;                   // first level that can merge (>= max(jmin, 1))
   int filter;                   // 1 when theta_dzs <= 1/sqrt(3) (geometric only)
   int criterion;                // DZS_CRIT_GEOMETRIC / DZS_CRIT_DYNAMICAL
   double rb;                    // R_lat + b_lat (dynamical)
@@ -90,7 +103,9 @@ __device__ __forceinline__ bool dynamical_merge(const MergeParams& mp, uint64_t 
 
 // ---- 4-channel uint64 exclusive prefix sums: k, k ux, k uy, k uz
 __global__ void k_prefix_totals(const int32_t* __restrict__ d_n, int64_t cap, const uint32_t* __restrict__ u,
-                                const uint32_t* __restrict__ k, uint64_t* __restrict__ tot) {
+                                const uint32_t* __restrict__ k, uint64_t* __restrict__ tot,
+                                const unsigned* __restrict__ need) {
+  if (!*need) return;
   const int64_t n = *d_n;
   int64_t base = (int64_t)blockIdx.x * kChunk;
   unsigned long long s[4] = {0, 0, 0, 0};
@@ -117,7 +132,8 @@ __global__ void k_prefix_totals(const int32_t* __restrict__ d_n, int64_t cap, co
 }
 
 // block c scans row c (channel c) of the chunk totals, 1024 at a time
-__global__ void k_prefix_scan_totals(uint64_t* __restrict__ tot, int nchunks) {
+__global__ void k_prefix_scan_totals(uint64_t* __restrict__ tot, int nchunks, const unsigned* __restrict__ need) {
+  if (!*need) return;
   __shared__ unsigned long long woff[32];
   __shared__ unsigned long long carry, block_total;
   uint64_t* row = tot + (int64_t)blockIdx.x * (nchunks + 1);
@@ -153,7 +169,8 @@ __global__ void k_prefix_scan_totals(uint64_t* __restrict__ tot, int nchunks) {
 
 __global__ void k_prefix_apply(const int32_t* __restrict__ d_n, int64_t cap, const uint32_t* __restrict__ u,
                                const uint32_t* __restrict__ k, const uint64_t* __restrict__ tot, int nchunks,
-                               uint64_t* __restrict__ pre) {
+                               uint64_t* __restrict__ pre, const unsigned* __restrict__ need) {
+  if (!*need) return;
   const int64_t n = *d_n;
   int64_t base = (int64_t)blockIdx.x * kChunk;
   if (base > n) return;
@@ -243,9 +260,48 @@ __device__ __forceinline__ int64_t gallop_up(const uint64_t* __restrict__ key, i
   return lower_bound_key(key, lo, hi, x);
 }
 
+// smallest index with a nonzero mark in this block, and whether any candidate
+// was deferred: one atomic each per block
+__device__ __forceinline__ void block_first(int64_t first, bool deferred, unsigned long long* __restrict__ first_slot,
+                                            unsigned* __restrict__ need) {
+  __shared__ unsigned long long wmin[32];
+  __shared__ int wdef[32];
+  unsigned long long f = (unsigned long long)first;
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long t = __shfl_down_sync(0xffffffffu, f, o);
+    f = t < f ? t : f;
+  }
+  const int d = __any_sync(0xffffffffu, deferred) ? 1 : 0;
+  if ((threadIdx.x & 31) == 0) {
+    wmin[threadIdx.x >> 5] = f;
+    wdef[threadIdx.x >> 5] = d;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long m = ~0ull;
+    int any = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      m = wmin[w] < m ? wmin[w] : m;
+      any |= wdef[w];
+    }
+    if (m != ~0ull) atomicMin(first_slot, m);
+    if (any) atomicOr(need, 1u);
+  }
+}
+
+// kPrefix false: the first pass over every particle (geometric criterion with
+// the member filter): candidates whose cells at the levels that can merge hold
+// at most kDirect particles are decided from direct sums, the others deferred.
+// kPrefix true (only when something was deferred, or without the filter):
+// the deferred particles (every particle without the filter) are decided from
+// the prefix sums.
+template <bool kPrefix>
 __global__ void k_merge_mark(const int32_t* __restrict__ d_n, int64_t cap, const uint64_t* __restrict__ key,
-                             const uint32_t* __restrict__ u, const uint64_t* __restrict__ pre,
-                             int32_t* __restrict__ mend, int32_t* __restrict__ keep, MergeParams mp) {
+                             const uint32_t* __restrict__ u, const uint32_t* __restrict__ kk,
+                             const uint64_t* __restrict__ pre, int32_t* __restrict__ mend,
+                             int32_t* __restrict__ keep, MergeParams mp, unsigned long long* __restrict__ first_slot,
+                             unsigned* __restrict__ need) {
+  if (kPrefix && !*need) return;
   const int64_t n = *d_n;
   const uint64_t* PK = pre;
   const uint64_t* PS = pre + (cap + 1);
@@ -255,15 +311,20 @@ __global__ void k_merge_mark(const int32_t* __restrict__ d_n, int64_t cap, const
     double amin2 = c ? __longlong_as_double((long long)~c) : __longlong_as_double(0x7ff0000000000000ll);
     rhs = __dmul_rn(mp.alpha, __dsqrt_rn(amin2));
   }
+  int64_t first = INT64_MAX;
+  bool deferred_any = false;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (kPrefix && mp.filter && mend[i] != kDeferred) continue;
     int32_t res = 0;
+    bool deferred = false;
     bool cand = true;
     if (mp.filter) cand = dist2_obs(u[i], u[cap + i], u[2 * cap + i]) > mp.rb2;
     if (cand) {
       uint64_t ki = key[i];
-      // candidate cells start at depth jmin: its bounds by galloping out from i
-      // (the coarser cells only contain it), deeper ones inside the previous
-      const int j0 = mp.jmin > 1 ? mp.jmin : 1;
+      // candidate cells start at depth jstart: its bounds by galloping out
+      // from i (the coarser cells only contain it), deeper ones inside the
+      // previous
+      const int j0 = mp.jstart;
       int64_t lo = 0, hi = n;
       for (int j = j0; j <= kMaxLevel; ++j) {
         int sh = 3 * (kMaxLevel - j);
@@ -280,11 +341,25 @@ __global__ void k_merge_mark(const int32_t* __restrict__ d_n, int64_t cap, const
         hi = e;
         if (e - s < 2) break;  // no finer cell holds two particles
         if (mp.criterion == DZS_CRIT_GEOMETRIC && mp.thr[j] == ~0ull) continue;
-        uint64_t K = PK[e] - PK[s];
+        uint64_t K = 0, S[3] = {0, 0, 0};
+        if (kPrefix) {
+          K = PK[e] - PK[s];
+          for (int ax = 0; ax < 3; ++ax)
+            S[ax] = PS[(int64_t)ax * (cap + 1) + e] - PS[(int64_t)ax * (cap + 1) + s];
+        } else {
+          if (e - s > kDirect) {
+            deferred = true;
+            break;
+          }
+          for (int64_t t = s; t < e; ++t) {
+            const uint64_t m = kk[t];
+            K += m;
+            for (int ax = 0; ax < 3; ++ax) S[ax] += m * u[ax * cap + t];
+          }
+        }
         uint64_t d2 = 0;
         for (int ax = 0; ax < 3; ++ax) {
-          uint64_t S = PS[(int64_t)ax * (cap + 1) + e] - PS[(int64_t)ax * (cap + 1) + s];
-          uint32_t com = (uint32_t)((2 * S + K) / (2 * K));
+          uint32_t com = (uint32_t)((2 * S[ax] + K) / (2 * K));
           int64_t off = (int32_t)(com - 0x80000000u);
           d2 += (uint64_t)(off * off);
         }
@@ -301,24 +376,29 @@ __global__ void k_merge_mark(const int32_t* __restrict__ d_n, int64_t cap, const
         }
       }
     }
-    mend[i] = res;
+    mend[i] = deferred ? kDeferred : res;
     keep[i] = res >= 0 ? 1 : 0;
+    if (res != 0 && i < first) first = i;
+    deferred_any = deferred_any || deferred;
   }
+  block_first(first, deferred_any, first_slot, need);
 }
 
+// the compacted state from the first changed particle on, into the spare
+// arrays (rank = exclusive scan of keep); merged cells summed directly
 template <class R>
 __global__ void k_merge_write(const int32_t* __restrict__ d_n, int64_t cap, const int32_t* __restrict__ mend,
                               const int32_t* __restrict__ rank, const uint64_t* __restrict__ key,
                               const uint32_t* __restrict__ u, const R* __restrict__ p,
                               const uint32_t* __restrict__ k, const uint32_t* __restrict__ id,
-                              const uint8_t* __restrict__ fl, const uint64_t* __restrict__ pre,
+                              const uint8_t* __restrict__ fl, const unsigned long long* __restrict__ first_slot,
                               uint64_t* __restrict__ key2, uint32_t* __restrict__ u2, R* __restrict__ p2,
                               uint32_t* __restrict__ k2, uint32_t* __restrict__ id2, uint8_t* __restrict__ fl2,
                               int32_t* __restrict__ d_n_out) {
   const int64_t n = *d_n;
-  const uint64_t* PK = pre;
-  const uint64_t* PS = pre + (cap + 1);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t first = *first_slot < (unsigned long long)n ? (int64_t)*first_slot : n;
+  for (int64_t i = first + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
     int32_t m = mend[i];
     if (m < 0) continue;
     int64_t j = rank[i];
@@ -334,13 +414,17 @@ __global__ void k_merge_write(const int32_t* __restrict__ d_n, int64_t cap, cons
       continue;
     }
     int64_t e = m;
-    uint64_t K = PK[e] - PK[i];
+    uint64_t K = 0;
+    for (int64_t t = i; t < e; ++t) K += k[t];
     uint32_t com[3];
     for (int ax = 0; ax < 3; ++ax) {
-      uint64_t S = PS[(int64_t)ax * (cap + 1) + e] - PS[(int64_t)ax * (cap + 1) + i];
-      com[ax] = (uint32_t)((2 * S + K) / (2 * K));
+      uint64_t S = 0;
       double acc = 0.0;  // left-to-right FP64 sum, no contraction
-      for (int64_t t = i; t < e; ++t) acc = __dadd_rn(acc, __dmul_rn((double)k[t], (double)p[ax * cap + t]));
+      for (int64_t t = i; t < e; ++t) {
+        S += (uint64_t)k[t] * u[ax * cap + t];
+        acc = __dadd_rn(acc, __dmul_rn((double)k[t], (double)p[ax * cap + t]));
+      }
+      com[ax] = (uint32_t)((2 * S + K) / (2 * K));
       u2[ax * cap + j] = com[ax];
       p2[ax * cap + j] = (R)(acc / (double)K);
     }
@@ -352,6 +436,30 @@ __global__ void k_merge_write(const int32_t* __restrict__ d_n, int64_t cap, cons
     fl2[j] = (uint8_t)(kFlMerged | kFlCrossed);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) *d_n_out = rank[n];
+}
+
+// the changed tail [first, n_new) back into the state arrays
+template <class R>
+__global__ void k_merge_copyback(const int32_t* __restrict__ d_n_new, int64_t cap,
+                                 const unsigned long long* __restrict__ first_slot, const uint64_t* __restrict__ key2,
+                                 const uint32_t* __restrict__ u2, const R* __restrict__ p2,
+                                 const uint32_t* __restrict__ k2, const uint32_t* __restrict__ id2,
+                                 const uint8_t* __restrict__ fl2, uint64_t* __restrict__ key, uint32_t* __restrict__ u,
+                                 R* __restrict__ p, uint32_t* __restrict__ k, uint32_t* __restrict__ id,
+                                 uint8_t* __restrict__ fl) {
+  const int64_t n = *d_n_new;
+  const int64_t first = *first_slot < (unsigned long long)n ? (int64_t)*first_slot : n;
+  for (int64_t i = first + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    for (int ax = 0; ax < 3; ++ax) {
+      u[ax * cap + i] = u2[ax * cap + i];
+      p[ax * cap + i] = p2[ax * cap + i];
+    }
+    key[i] = key2[i];
+    k[i] = k2[i];
+    id[i] = id2[i];
+    fl[i] = fl2[i];
+  }
 }
 
 }  // namespace
@@ -371,17 +479,23 @@ void launch_amin2(dzs_ctx* c) {
 
 // the dynamical criterion reads a_min^2 from counters[14] (launch_amin2 first)
 void launch_merge(dzs_ctx* c, uint64_t rlat) {
-  c->launches += 8;
   const bool dyn = c->P.dzs_criterion == DZS_CRIT_DYNAMICAL;
   Buffers& B = c->B;
   MergeParams mp;
-  for (int j = 0; j <= kMaxLevel; ++j)
-    mp.thr[j] = (c->merge_thr[j] == ~0ull) ? ~0ull : rlat + c->merge_thr[j];
-  for (int j = 0; j <= kMaxLevel; ++j)
-    if (mp.thr[j] != ~0ull && mp.thr[j] >= 4294967296ull) mp.thr[j] = ~0ull;
+  // a COM offset from the observer is below 2^31 per axis: d^2 <= 3 * 2^62,
+  // so a level with T_j^2 >= 3 * 2^62 never merges
+  const uint64_t d2max = 3ull << 62;
+  for (int j = 0; j <= kMaxLevel; ++j) {
+    uint64_t t = (c->merge_thr[j] == ~0ull) ? ~0ull : rlat + c->merge_thr[j];
+    if (t != ~0ull && (t >= 4294967296ull || t * t >= d2max)) t = ~0ull;
+    mp.thr[j] = t;
+  }
   uint64_t rb = rlat + c->blat;
   mp.rb2 = (rb >= 4294967296ull) ? ~0ull : rb * rb;
   mp.jmin = c->jmin;
+  mp.jstart = c->jmin > 1 ? c->jmin : 1;
+  if (!dyn)
+    while (mp.jstart <= kMaxLevel && mp.thr[mp.jstart] == ~0ull) ++mp.jstart;
   mp.filter = (!dyn && c->P.theta_dzs <= 0.5773502691896257) ? 1 : 0;
   mp.criterion = c->P.dzs_criterion;
   mp.rb = (double)rb;
@@ -394,32 +508,48 @@ void launch_merge(dzs_ctx* c, uint64_t rlat) {
   }
   uint64_t* slot = c->B.counters + 14;
   mp.amin2_slot = slot;
+  unsigned long long* first = (unsigned long long*)(c->B.counters + 22);
+  unsigned* need = (unsigned*)(c->B.counters + 23);
+  cudaMemsetAsync(first, 0xff, sizeof(uint64_t), c->stream);
   int nchunks = (int)((c->cap + kChunk) / kChunk);
   uint64_t* tot = (uint64_t*)B.blocksum;
-  k_prefix_totals<<<nchunks, 256, 0, c->stream>>>(B.n, c->cap, B.u, B.k, tot);
-  k_prefix_scan_totals<<<4, 1024, 0, c->stream>>>(tot, nchunks);
-  k_prefix_apply<<<nchunks, 256, 0, c->stream>>>(B.n, c->cap, B.u, B.k, tot, nchunks, B.prefix);
   int32_t* keep = B.iscan + (c->cap + 1);
   int32_t* rank = B.iscan;
   int grid = grid_for(c->N0);
-  k_merge_mark<<<grid, kThreads, 0, c->stream>>>(B.n, c->cap, B.key, B.u, B.prefix, B.mend, keep, mp);
+  if (mp.filter) {
+    c->launches += 1;
+    cudaMemsetAsync(need, 0, sizeof(unsigned), c->stream);
+    k_merge_mark<false><<<grid, kThreads, 0, c->stream>>>(B.n, c->cap, B.key, B.u, B.k, B.prefix, B.mend, keep, mp,
+                                                          first, need);
+  } else {
+    cudaMemsetAsync(need, 1, sizeof(unsigned), c->stream);  // nonzero: every particle takes the prefix pass
+  }
+  // prefix sums and the second mark pass: they return at once unless needed
+  c->launches += 4;
+  k_prefix_totals<<<nchunks, 256, 0, c->stream>>>(B.n, c->cap, B.u, B.k, tot, need);
+  k_prefix_scan_totals<<<4, 1024, 0, c->stream>>>(tot, nchunks, need);
+  k_prefix_apply<<<nchunks, 256, 0, c->stream>>>(B.n, c->cap, B.u, B.k, tot, nchunks, B.prefix, need);
+  k_merge_mark<true><<<grid, kThreads, 0, c->stream>>>(B.n, c->cap, B.key, B.u, B.k, B.prefix, B.mend, keep, mp,
+                                                       first, need);
+  c->launches += 5;
   exclusive_scan_i32(c, keep, rank, B.n, c->cap);
-  if (c->fp64)
+  if (c->fp64) {
     k_merge_write<double><<<grid, kThreads, 0, c->stream>>>(
-        B.n, c->cap, B.mend, rank, B.key, B.u, (const double*)B.p, B.k, B.id, B.fl, B.prefix, B.key2, B.u2,
+        B.n, c->cap, B.mend, rank, B.key, B.u, (const double*)B.p, B.k, B.id, B.fl, first, B.key2, B.u2,
         (double*)B.p2, B.k2, B.id2, B.fl2, B.n + 1);
-  else
+    k_merge_copyback<double><<<grid, kThreads, 0, c->stream>>>(B.n + 1, c->cap, first, B.key2, B.u2,
+                                                               (const double*)B.p2, B.k2, B.id2, B.fl2, B.key, B.u,
+                                                               (double*)B.p, B.k, B.id, B.fl);
+  } else {
     k_merge_write<float><<<grid, kThreads, 0, c->stream>>>(
-        B.n, c->cap, B.mend, rank, B.key, B.u, (const float*)B.p, B.k, B.id, B.fl, B.prefix, B.key2, B.u2,
+        B.n, c->cap, B.mend, rank, B.key, B.u, (const float*)B.p, B.k, B.id, B.fl, first, B.key2, B.u2,
         (float*)B.p2, B.k2, B.id2, B.fl2, B.n + 1);
+    k_merge_copyback<float><<<grid, kThreads, 0, c->stream>>>(B.n + 1, c->cap, first, B.key2, B.u2,
+                                                              (const float*)B.p2, B.k2, B.id2, B.fl2, B.key, B.u,
+                                                              (float*)B.p, B.k, B.id, B.fl);
+  }
   // new count staged in n[1] (every thread of the write kernel read n[0])
   cudaMemcpyAsync(B.n, B.n + 1, sizeof(int32_t), cudaMemcpyDeviceToDevice, c->stream);
-  std::swap(B.key, B.key2);
-  std::swap(B.u, B.u2);
-  std::swap(B.p, B.p2);
-  std::swap(B.k, B.k2);
-  std::swap(B.id, B.id2);
-  std::swap(B.fl, B.fl2);
 }
 
 }  // namespace dzs

@@ -14,7 +14,13 @@
 // cells around the group's depth-f cell (or the shallower leaves covering
 // them, each once): the same nodes are tested and the same interaction set is
 // built, without the first rounds of the descent.  Groups above depth f start
-// at the root.  Per node:
+// at the root.  Deeper still, a group at depth >= F - 1 (F = f + 2, else
+// f + 1: at most 6 depth-F cells per axis) starts from the depth-F nodes of
+// the cells within r_cut of its cube along every axis, when each of their
+// ancestors between f and F is "always opened" (its COM is close enough to
+// its cube centre that every group cube within r_cut of the node opens it):
+// the walk from f would open or skip those ancestors, so again the same nodes
+// are tested; otherwise the group falls back to the depth-f cells.  Per node:
 //   skip   the node's cube is farther than r_cut from the group cube;
 //   open   the cubes touch, or l_n >= theta d(COM_n, group cube);
 //   accept otherwise: the monopole (COM, mass, softening) joins the list,

@@ -178,8 +178,11 @@ def test_pm_mesh_delta(dzs):
 # ---------------------------------------------------------------- merge
 
 @pytest.mark.parametrize("precision", [1, 0])
-@pytest.mark.parametrize("upto,rfrac", [(70, None), (90, None), (50, 0.05)])
+@pytest.mark.parametrize("upto,rfrac", [(70, None), (90, None), (50, 0.05), (70, 0.5), (90, 0.6)])
 def test_merge_bit_exact(dzs, precision, upto, rfrac):
+    """many candidates (radius from the step's table, or 0.05 L) and few
+    (0.5 L, 0.6 L: ~1300 and ~300 particles beyond R + b, cells of at most a
+    few dozen particles, which the first mark pass sums directly)"""
     kw = dict(SMALL, dzs_on=0)  # an un-merged evolved state
     st = oracle_run(kw, upto)
     P = oparams(**SMALL)
@@ -200,6 +203,26 @@ def test_merge_bit_exact(dzs, precision, upto, rfrac):
         assert np.array_equal(got["p"], want["p"])
     else:
         assert np.array_equal(got["p"], want["p"].astype(np.float32).astype(np.float64))
+
+
+def test_merge_nothing_qualifies_leaves_the_state(dzs):
+    """radius 0.7 L: a few dozen particles lie beyond R + b, no cell qualifies;
+    the state comes back unchanged, as from the oracle"""
+    kw = dict(SMALL, dzs_on=0)
+    st = dict(oracle_run(kw, 70))
+    st["fl"] = st["fl"] | O.FL_CROSSED
+    P = oparams(**SMALL)
+    rlat = int(0.7 * TWO32)
+    want = O.merge(P, rlat, st)
+    assert want["u"].shape[1] == st["u"].shape[1]
+    with dzs.Context(**dict(SMALL, precision=1)) as ctx:
+        ctx.set_state(st, 70)
+        before = ctx.state()
+        ctx.merge_only(rlat)
+        got = ctx.state()
+    for name in ("u", "k", "id", "fl", "p"):
+        assert np.array_equal(got[name], want[name]), name
+        assert np.array_equal(got[name], before[name]), name
 
 
 # ---------------------------------------------------------------- kick, drift, crossing
