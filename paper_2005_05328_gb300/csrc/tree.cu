@@ -319,11 +319,28 @@ __global__ void k_tree_up_all(const int32_t* __restrict__ lvl, int64_t cap, cons
     if (nd.child >= 0) continue;  // finished by its last child
     uint64_t K = 0, S[3] = {0, 0, 0};
     uint32_t kmax = 0;
-    for (int64_t i = nd.start; i < (int64_t)nd.start + nd.count; ++i) {
-      uint32_t kk = k[i];
-      K += kk;
-      kmax = max(kmax, kk);
-      for (int ax = 0; ax < 3; ++ax) S[ax] += (uint64_t)kk * u[ax * cap + i];
+    // four particles per iteration, their loads issued together (a leaf holds
+    // <= B particles, a depth-21 leaf possibly more)
+    const int64_t i1 = (int64_t)nd.start + nd.count;
+    for (int64_t i0 = nd.start; i0 < i1; i0 += 4) {
+      uint32_t kk[4], ux[4], uy[4], uz[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const bool in = i0 + q < i1;
+        const int64_t i = in ? i0 + q : i0;
+        kk[q] = in ? k[i] : 0u;
+        ux[q] = u[i];
+        uy[q] = u[cap + i];
+        uz[q] = u[2 * cap + i];
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        K += kk[q];
+        kmax = max(kmax, kk[q]);
+        S[0] += (uint64_t)kk[q] * ux[q];
+        S[1] += (uint64_t)kk[q] * uy[q];
+        S[2] += (uint64_t)kk[q] * uz[q];
+      }
     }
     write_node_sums(nodes, nsum, node_cap, t, K, S, kmax);
     int64_t cur = t;
@@ -338,11 +355,15 @@ __global__ void k_tree_up_all(const int32_t* __restrict__ lvl, int64_t cap, cons
       const int32_t c0 = nodes[par].child;
       uint64_t PK = 0, PS[3] = {0, 0, 0};
       uint32_t pkmax = 0;
-      for (int q = 0; q < nch; ++q) {
-        const int64_t ci = (int64_t)c0 + q;
-        PK += __ldcg(&nodes[ci].mass);
-        pkmax = max(pkmax, __ldcg(&nodes[ci].kmax));
-        for (int ax = 0; ax < 3; ++ax) PS[ax] += __ldcg(&nsum[ax * node_cap + ci]);
+      // the (<= 8) children's sums, all loads issued together
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        if (q < nch) {
+          const int64_t ci = (int64_t)c0 + q;
+          PK += __ldcg(&nodes[ci].mass);
+          pkmax = max(pkmax, __ldcg(&nodes[ci].kmax));
+          for (int ax = 0; ax < 3; ++ax) PS[ax] += __ldcg(&nsum[ax * node_cap + ci]);
+        }
       }
       write_node_sums(nodes, nsum, node_cap, par, PK, PS, pkmax);
       cur = par;

@@ -425,11 +425,15 @@ __global__ void k_front_fill(const int32_t* __restrict__ lvl, const Node* __rest
 // sqrt(skip_d2) + (distance from the COM to the farthest corner of a's cube),
 // and that passes the open test of a's depth.  Below always-opened ancestors
 // the per-group walk reaches exactly the depth-F nodes within r_cut.
-struct OpenD2 {
-  uint64_t v[kMaxLevel + 1];
+// far2max[l]: largest squared COM-to-farthest-corner distance of a depth-l
+// node that is always opened, (sqrt(open_d2[l]) - sqrt(skip_d2))^2 shrunk by a
+// relative 2^-12 so that the FP32 sum below decides on the safe side (-1:
+// never; +inf: the threshold opens at every distance)
+struct FarMax {
+  float v[kMaxLevel + 1];
 };
 __global__ void k_front_fill_F(const int32_t* __restrict__ lvl, const Node* __restrict__ nodes,
-                               const int32_t* __restrict__ parent, int f, int F, double skip_r, OpenD2 open_d2,
+                               const int32_t* __restrict__ parent, int f, int F, FarMax far2max,
                                int32_t* __restrict__ ftab, uint8_t* __restrict__ fspan) {
   int64_t nF = 0;
   for (int j = 0; j <= F; ++j) nF += lvl[j];
@@ -443,17 +447,15 @@ __global__ void k_front_fill_F(const int32_t* __restrict__ lvl, const Node* __re
       const Node an = nodes[a];
       const int ja = (int)(an.meta & 0xff);
       if (ja < f) break;  // above f no node is ever accepted
-      const uint64_t od = open_d2.v[ja];
-      if (od == ~0ull) continue;  // opens at every distance
-      const double ha = (double)(1u << (31 - ja));
-      double far2 = 0.0;
+      const float ha = (float)(1u << (31 - ja));
+      float far2 = 0.f;
       const uint32_t cm[3] = {an.comx, an.comy, an.comz}, cn[3] = {an.cx, an.cy, an.cz};
+#pragma unroll
       for (int q = 0; q < 3; ++q) {
-        const double d = fabs((double)(int32_t)(cm[q] - cn[q])) + ha;
-        far2 += d * d;
+        const float d = (float)abs((int32_t)(cm[q] - cn[q])) + ha;
+        far2 = fmaf(d, d, far2);
       }
-      const double bound = skip_r + sqrt(far2);
-      if (!(bound * bound * (1.0 + 1e-9) + 4.0 <= (double)od)) may_accept = true;
+      if (!(far2 <= far2max.v[ja])) may_accept = true;
     }
     const int span = 1 << (F - j);
     const uint32_t h = j == 0 ? 0x80000000u : (1u << (31 - j));
@@ -890,11 +892,18 @@ void walk_impl(dzs_ctx* c, bool tree, bool close_kick, int step) {
       c->launches += 1;
       cudaMemsetAsync((void*)C.ftabF, 0xff, sizeof(int32_t) * cellsF, c->stream);
       cudaMemsetAsync((void*)C.fspanF, 0, (size_t)cellsF, c->stream);
-      OpenD2 od;
-      for (int l = 0; l <= kMaxLevel; ++l) od.v[l] = C.open_d2[l];
+      FarMax fm;
+      const double skip_r = std::sqrt((double)C.skip_d2) * (1.0 + 1e-12);
+      for (int l = 0; l <= kMaxLevel; ++l) {
+        if (C.open_d2[l] == ~0ull) {
+          fm.v[l] = INFINITY;
+          continue;
+        }
+        const double room = std::sqrt((double)C.open_d2[l]) * (1.0 - 1e-12) - skip_r;
+        fm.v[l] = room > 0.0 ? (float)(room * room * (1.0 - 0x1p-12)) : -1.0f;
+      }
       k_front_fill_F<<<grid_for(cellsF, kThreads, 4), kThreads, 0, c->stream>>>(
-          c->B.lvl_count, c->B.nodes, c->B.parent, C.front, C.frontF, std::sqrt((double)C.skip_d2), od,
-          (int32_t*)C.ftabF, (uint8_t*)C.fspanF);
+          c->B.lvl_count, c->B.nodes, c->B.parent, C.front, C.frontF, fm, (int32_t*)C.ftabF, (uint8_t*)C.fspanF);
     }
   }
   // automatic: the range-masked evaluation when the walk groups of a uniform
