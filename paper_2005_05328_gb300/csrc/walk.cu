@@ -170,11 +170,29 @@ struct WalkConst {
   int frontF;                 // window frontier depth F > f (0: none)
   uint32_t rcx;               // largest integer gap with gap^2 <= skip_d2
   const int32_t* ftabF;       // [2^F]^3: node of each depth-F cell (or the leaf above it), -1 if empty
+  const unsigned long long* hmax;  // bits of the largest spline radius of any merged particle or node (device)
+  R h0;                            // spline radius of multiplicity 1
   const uint8_t* fspanF;      // its F - depth, bit 7: an ancestor at depths [f, F) may accept
 };
 
 __device__ __forceinline__ uint64_t exact_d2(const uint32_t (&v)[3]) {
   return (uint64_t)v[0] * v[0] + (uint64_t)v[1] * v[1] + (uint64_t)v[2] * v[2];
+}
+
+// FP32: no division (1/h by the hardware reciprocal approximation, 1/q = h / r
+// from the rsqrt the pair already has) and no slow path, so that the rarely
+// taken branch adds little to the pair loop
+__device__ __forceinline__ float rcp_approx(float v) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(v));
+  return y;
+}
+__device__ __forceinline__ float spline_fac_ir(float r, float ir, float h) {
+  const float ih = rcp_approx(h), q = r * ih, ih3 = ih * ih * ih;
+  if (q < 0.5f) return fmaf(q * q, fmaf(32.0f, q, -38.4f), 32.0f / 3.0f) * ih3;
+  const float iq = h * ir, iq3 = iq * iq * iq;
+  const float poly = fmaf(q, fmaf(q, fmaf(q, -32.0f / 3.0f, 38.4f), -48.0f), 64.0f / 3.0f);
+  return fmaf(-1.0f / 15.0f, iq3, poly) * ih3;
 }
 
 template <class R>
@@ -245,12 +263,22 @@ __device__ __forceinline__ bool in_range(double r2, double rcut2) { return r2 < 
 // force of one entry at offset (dx, dy, dz), 0 < r^2 < r_cut^2 (the caller
 // has tested the range)
 template <class R>
-__device__ __forceinline__ void pair_force(R dx, R dy, R dz, R r2, R m, R he, R hi, const WalkConst<R>& C, R& ax,
-                                           R& ay, R& az) {
+__device__ __forceinline__ void pair_force(R dx, R dy, R dz, R r2, R m, const R* hep, R hi, R hmax,
+                                           const WalkConst<R>& C, R& ax, R& ay, R& az) {
   R r, ir;
   inv_and_r(r2, r, ir);
-  const R h = he > hi ? he : hi;
-  const R fac = (r >= h) ? ir * ir * ir : spline_fac(r, h);
+  R fac = ir * ir * ir;
+  // the entry's spline radius is read only when some softening of this step
+  // reaches r (hmax: the largest radius of any particle or node)
+  if (r < hmax) {
+    const R he = *hep, h = he > hi ? he : hi;
+    if (r < h) {
+      if (sizeof(R) == 4)
+        fac = (R)spline_fac_ir((float)r, (float)ir, (float)h);
+      else
+        fac = spline_fac(r, h);
+    }
+  }
   R sfac;
   if (sizeof(R) == 4 && C.poly) {
     const float t = fmaf((float)r, (float)C.tcoef, -1.0f);
@@ -268,11 +296,11 @@ __device__ __forceinline__ void pair_force(R dx, R dy, R dz, R r2, R m, R he, R 
 }
 
 template <class R>
-__device__ __forceinline__ void pair_in_range(const LEntry<R>& E, R he, const Pos<R>& P, R hi,
+__device__ __forceinline__ void pair_in_range(const LEntry<R>& E, const R* hep, const Pos<R>& P, R hi, R hmax,
                                               const WalkConst<R>& C, R& ax, R& ay, R& az) {
   R dx, dy, dz;
   const R r2 = entry_r2(E, P, dx, dy, dz);
-  pair_force(dx, dy, dz, r2, E.m, he, hi, C, ax, ay, az);
+  pair_force(dx, dy, dz, r2, E.m, hep, hi, hmax, C, ax, ay, az);
 }
 
 // Evaluate the list [0, len) for this lane's particle: the lane takes every
@@ -282,24 +310,24 @@ __device__ __forceinline__ void pair_in_range(const LEntry<R>& E, R he, const Po
 // only and the warp iterates as often as its busiest lane has pairs in range.
 template <class R, bool kMasked>
 __device__ __forceinline__ void eval_list(const WalkSmem<R>& sm, int w, int len, int sub, int Sm, const Pos<R>& P,
-                                          R hi, const WalkConst<R>& C, R& ax, R& ay, R& az, unsigned& nin) {
+                                          R hi, R hmax, const WalkConst<R>& C, R& ax, R& ay, R& az,
+                                          unsigned& nin) {
   if (!kMasked) {
     // most entries in range (a group cube small against r_cut): one pass,
     // the force arithmetic guarded by the range test
     int e = sub;
     for (; e + Sm < len; e += 2 * Sm) {  // two entries per iteration (independent chains)
       const LEntry<R> E0 = sm.e[w][e], E1 = sm.e[w][e + Sm];
-      const R h0 = sm.h[w][e], h1 = sm.h[w][e + Sm];
       R dx0, dy0, dz0, dx1, dy1, dz1;
       const R r0 = entry_r2(E0, P, dx0, dy0, dz0);
       const R r1 = entry_r2(E1, P, dx1, dy1, dz1);
       if (in_range(r0, C.rcut2)) {
         ++nin;
-        pair_force(dx0, dy0, dz0, r0, E0.m, h0, hi, C, ax, ay, az);
+        pair_force(dx0, dy0, dz0, r0, E0.m, &sm.h[w][e], hi, hmax, C, ax, ay, az);
       }
       if (in_range(r1, C.rcut2)) {
         ++nin;
-        pair_force(dx1, dy1, dz1, r1, E1.m, h1, hi, C, ax, ay, az);
+        pair_force(dx1, dy1, dz1, r1, E1.m, &sm.h[w][e + Sm], hi, hmax, C, ax, ay, az);
       }
     }
     if (e < len) {
@@ -308,7 +336,7 @@ __device__ __forceinline__ void eval_list(const WalkSmem<R>& sm, int w, int len,
       const R r2 = entry_r2(E0, P, dx, dy, dz);
       if (in_range(r2, C.rcut2)) {
         ++nin;
-        pair_force(dx, dy, dz, r2, E0.m, sm.h[w][e], hi, C, ax, ay, az);
+        pair_force(dx, dy, dz, r2, E0.m, &sm.h[w][e], hi, hmax, C, ax, ay, az);
       }
     }
     return;
@@ -331,7 +359,7 @@ __device__ __forceinline__ void eval_list(const WalkSmem<R>& sm, int w, int len,
         const int k = __ffs(mask) - 1;
         mask &= mask - 1u;
         const int e = sub + (kb + k) * Sm;
-        pair_in_range(sm.e[w][e], sm.h[w][e], P, hi, C, ax, ay, az);
+        pair_in_range(sm.e[w][e], &sm.h[w][e], P, hi, hmax, C, ax, ay, az);
       }
     }
   }
@@ -367,17 +395,28 @@ __device__ __forceinline__ int warp_incl_scan(int v, int lane) {
   return v;
 }
 
+__device__ __forceinline__ unsigned long long radius_bits(float v) { return __float_as_uint(v); }
+__device__ __forceinline__ unsigned long long radius_bits(double v) { return (unsigned long long)__double_as_longlong(v); }
+template <class R>
+__device__ __forceinline__ R radius_of(unsigned long long b);
+template <>
+__device__ __forceinline__ float radius_of<float>(unsigned long long b) { return __uint_as_float((unsigned)b); }
+template <>
+__device__ __forceinline__ double radius_of<double>(unsigned long long b) { return __longlong_as_double((long long)b); }
+
 // per-step walk inputs: packed particle entries (position, G m / s^2) and spline
 // radius, node spline radius
 template <class R>
 __global__ void k_walk_prep(const int32_t* __restrict__ d_n, int64_t cap, const uint32_t* __restrict__ u,
                             const uint32_t* __restrict__ k, const int32_t* __restrict__ lvl,
                             const Node* __restrict__ nodes, Entry<R>* __restrict__ pm,
-                            R* __restrict__ ph, R* __restrict__ nh, R gm0, R h0) {
+                            R* __restrict__ ph, R* __restrict__ nh, R gm0, R h0,
+                            unsigned long long* __restrict__ hmax_bits) {
   const int64_t n = *d_n;
   int64_t nn = 0;
   for (int j = 0; j <= kMaxLevel; ++j) nn += lvl[j];
   const int64_t m = n > nn ? n : nn;
+  uint32_t kbig = 1;  // largest multiplicity seen (radius h0 k^(1/3) grows with it)
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
     if (i < n) {
       uint32_t kk = k[i];
@@ -388,11 +427,18 @@ __global__ void k_walk_prep(const int32_t* __restrict__ d_n, int64_t cap, const 
       E.m = gm0 * (R)kk;
       pm[i] = E;
       ph[i] = kk == 1 ? h0 : h0 * cbrt((R)kk);
+      kbig = max(kbig, kk);
     }
     if (i < nn) {
       uint32_t km = nodes[i].kmax;
       nh[i] = km == 1 ? h0 : h0 * cbrt((R)km);
+      kbig = max(kbig, km);
     }
+  }
+  kbig = __reduce_max_sync(0xffffffffu, kbig);
+  if ((threadIdx.x & 31) == 0 && kbig > 1) {
+    const R hb = h0 * cbrt((R)kbig);  // the same expression as the radii above
+    atomicMax(hmax_bits, radius_bits(hb));
   }
 }
 
@@ -491,6 +537,8 @@ __global__ void __launch_bounds__(kWarps * 32, sizeof(R) == 4 ? 7 : 5) k_walk(
   int maxtop = 0;  // deepest stack use of this warp (diagnostic)
   unsigned ntests = 0, nrounds = 0;  // node tests and traversal rounds of this warp (diagnostic)
   unsigned nwin = 0, nfall = 0;      // group passes started from the depth-F window, and fallbacks
+  // no spline radius of this step exceeds hmax (h0 unless something merged)
+  const R hmax = max(C.h0, radius_of<R>(*C.hmax));
   for (;;) {
     int gi = 0;
     if (lane == 0) gi = (int)atomicAdd(next, 1u);
@@ -587,7 +635,7 @@ __global__ void __launch_bounds__(kWarps * 32, sizeof(R) == 4 ? 7 : 5) k_walk(
 #define DZS_WALK_FLUSH()                                                     \
   do {                                                                       \
     __syncwarp();                                                            \
-    eval_list<R, kMasked>(sm, w, len, sub, Sm, P, hi, C, ax, ay, az, nin);      \
+    eval_list<R, kMasked>(sm, w, len, sub, Sm, P, hi, hmax, C, ax, ay, az, nin); \
     if (lane == 0) npairs += (unsigned)len * (unsigned)cnt;                  \
     glen += len;                                                             \
     len = 0;                                                                 \
@@ -878,9 +926,12 @@ void walk_impl(dzs_ctx* c, bool tree, bool close_kick, int step) {
   Entry<R>* pm = (Entry<R>*)c->B.wpm;
   R* ph = (R*)c->B.wph;
   R* nh = (R*)c->B.wnh;
+  C.h0 = (R)(2.8 * c->eps0 / s);
+  unsigned long long* hmax_slot = (unsigned long long*)(c->B.counters + 24);
+  C.hmax = hmax_slot;
+  cudaMemsetAsync(hmax_slot, 0, sizeof(uint64_t), c->stream);
   k_walk_prep<R><<<grid_for(c->node_cap), kThreads, 0, c->stream>>>(c->B.n, c->cap, c->B.u, c->B.k, c->B.lvl_count,
-                                                                     c->B.nodes, pm, ph, nh, C.gm0,
-                                                                     (R)(2.8 * c->eps0 / s));
+                                                                     c->B.nodes, pm, ph, nh, C.gm0, C.h0, hmax_slot);
   if (C.front > 0 && tree) {
     const int64_t cells = (int64_t)1 << (3 * C.front);
     c->launches += 1;
