@@ -35,7 +35,7 @@
 // threshold, where the uint64 sum decides) and builds the same interaction
 // set as the CPU reference, with no FP64 in the traversal.
 // The list lives in shared memory and is evaluated between rounds, when it
-// holds more than 236 entries (a round adds at most 32 monopoles and the
+// holds more than 172 entries (a round adds at most 32 monopoles and the
 // leaves that fit; leaves that do not fit wait on the stack).  A group of c
 // particles puts every lane to work: lane -> particle m = lane mod c, the
 // S_m lanes of particle m each taking every S_m-th entry.  Entries are taken
@@ -54,12 +54,13 @@
 namespace dzs {
 namespace {
 
-// shared memory sets the occupancy (7 blocks of 4 warps per SM, 72 registers
-// in FP32): stack 512 entries (deepest use measured 308; an overflow sets an
-// error bit), list 300 entries
+// shared memory sets the occupancy (8 blocks of 4 warps per SM in FP32, 64
+// registers): stack 512 entries (deepest use measured 308; an overflow sets an
+// error bit), list 236 entries (8 blocks measured 2% faster than 7 blocks
+// with 300-entry lists)
 constexpr int kWarps = 4;
 constexpr int kStack = 512;
-constexpr int kList = 300;
+constexpr int kList = 236;
 
 // Q(t) power-series coefficients, t = 2 x / 2.5 - 1; FP32 rel. error 3.32e-07
 // (generated by gen_split_poly.py)
@@ -226,8 +227,9 @@ __device__ __forceinline__ double split_factor(double x, int) {
   return erfc(x) + 1.1283791670955126 * x * exp(-x * x);
 }
 
+// r^2 >= 1 lattice unit^2 here (no denormals): the plain hardware rsqrt
 __device__ __forceinline__ void inv_and_r(float r2, float& r, float& ir) {
-  ir = rsqrtf(r2);
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(ir) : "f"(r2));
   r = r2 * ir;
 }
 __device__ __forceinline__ void inv_and_r(double r2, double& r, double& ir) {
@@ -522,7 +524,7 @@ __global__ void k_front_fill_F(const int32_t* __restrict__ lvl, const Node* __re
 // listed entries lie beyond r_cut of a given particle: groups not small
 // against r_cut), else with one range-guarded pass
 template <class R, bool kMasked>
-__global__ void __launch_bounds__(kWarps * 32, sizeof(R) == 4 ? 7 : 5) k_walk(
+__global__ void __launch_bounds__(kWarps * 32, sizeof(R) == 4 ? 8 : 5) k_walk(
     const int32_t* __restrict__ groups, const uint64_t* __restrict__ counters, unsigned int* __restrict__ next,
     const Node* __restrict__ nodes, const R* __restrict__ nh, int64_t cap, const uint32_t* __restrict__ u,
     const Entry<R>* __restrict__ pm, const R* __restrict__ ph, R* __restrict__ p, R* __restrict__ g, WalkConst<R> C,
