@@ -81,14 +81,16 @@ struct Tables {
 };
 
 // node record of the oct-tree, 48 bytes
+// the first 32 bytes hold what the tree walk reads per node test (the cube
+// centre follows from the COM, which lies in the cube, and the level)
 struct Node {
-  uint32_t cx, cy, cz;        // cube centre (lattice)
   uint32_t comx, comy, comz;  // rounded integer centre of mass
   uint32_t mass;              // sum of k
-  uint32_t kmax;              // largest member k (softening)
   int32_t start, count;       // particle range
   int32_t child;              // first child, -1 for a leaf
   uint32_t meta;              // level (bits 0-7) | nchild (bits 8-15)
+  uint32_t cx, cy, cz;        // cube centre (lattice)
+  uint32_t kmax;              // largest member k (softening)
 };
 static_assert(sizeof(Node) == 48, "node layout");
 

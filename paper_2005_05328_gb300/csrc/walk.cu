@@ -666,8 +666,10 @@ __global__ void __launch_bounds__(kWarps * 32, sizeof(R) == 4 ? 8 : 5) k_walk(
             // uint64 sum decides -- the same decision as the integer rule
             uint32_t gp[3], dmv[3];
             float d2f = 0.f, c2f = 0.f;
-            const uint32_t cn[3] = {nd.cx, nd.cy, nd.cz};
             const uint32_t cm[3] = {nd.comx, nd.comy, nd.comz};
+            // cube centre from the COM (inside the cube) and the level
+            const uint32_t hn = 1u << (31 - nlevel), cmask = ~((hn << 1) - 1u);
+            const uint32_t cn[3] = {(cm[0] & cmask) | hn, (cm[1] & cmask) | hn, (cm[2] & cmask) | hn};
             // gap = max(|dc|, h) - h; the root touches everything (h = max)
             const uint32_t h = nlevel == 0 ? 0xffffffffu : hg + (1u << (31 - nlevel));
 #pragma unroll
