@@ -223,6 +223,9 @@ void launch_keys(dzs_ctx* c);
 void launch_unpermute(dzs_ctx* c, double* g_out);
 void launch_close_kick(dzs_ctx* c, int step);
 void launch_merge(dzs_ctx* c, uint64_t rlat);
+// exclusive uint64 prefix sums of k, k ux, k uy, k uz over the particles into
+// B.prefix ([4][cap + 1])
+void launch_mass_prefix(dzs_ctx* c);
 void launch_amin2(dzs_ctx* c);
 void launch_tree(dzs_ctx* c);
 void launch_cell_start(dzs_ctx* c);

@@ -105,7 +105,7 @@ __device__ __forceinline__ bool dynamical_merge(const MergeParams& mp, uint64_t 
 __global__ void k_prefix_totals(const int32_t* __restrict__ d_n, int64_t cap, const uint32_t* __restrict__ u,
                                 const uint32_t* __restrict__ k, uint64_t* __restrict__ tot,
                                 const unsigned* __restrict__ need) {
-  if (!*need) return;
+  if (need && !*need) return;
   const int64_t n = *d_n;
   int64_t base = (int64_t)blockIdx.x * kChunk;
   unsigned long long s[4] = {0, 0, 0, 0};
@@ -133,7 +133,7 @@ __global__ void k_prefix_totals(const int32_t* __restrict__ d_n, int64_t cap, co
 
 // block c scans row c (channel c) of the chunk totals, 1024 at a time
 __global__ void k_prefix_scan_totals(uint64_t* __restrict__ tot, int nchunks, const unsigned* __restrict__ need) {
-  if (!*need) return;
+  if (need && !*need) return;
   __shared__ unsigned long long woff[32];
   __shared__ unsigned long long carry, block_total;
   uint64_t* row = tot + (int64_t)blockIdx.x * (nchunks + 1);
@@ -170,7 +170,7 @@ __global__ void k_prefix_scan_totals(uint64_t* __restrict__ tot, int nchunks, co
 __global__ void k_prefix_apply(const int32_t* __restrict__ d_n, int64_t cap, const uint32_t* __restrict__ u,
                                const uint32_t* __restrict__ k, const uint64_t* __restrict__ tot, int nchunks,
                                uint64_t* __restrict__ pre, const unsigned* __restrict__ need) {
-  if (!*need) return;
+  if (need && !*need) return;
   const int64_t n = *d_n;
   int64_t base = (int64_t)blockIdx.x * kChunk;
   if (base > n) return;
@@ -463,6 +463,16 @@ __global__ void k_merge_copyback(const int32_t* __restrict__ d_n_new, int64_t ca
 }
 
 }  // namespace
+
+void launch_mass_prefix(dzs_ctx* c) {
+  c->launches += 3;
+  Buffers& B = c->B;
+  const int nchunks = (int)((c->cap + kChunk) / kChunk);
+  uint64_t* tot = (uint64_t*)B.blocksum;
+  k_prefix_totals<<<nchunks, 256, 0, c->stream>>>(B.n, c->cap, B.u, B.k, tot, nullptr);
+  k_prefix_scan_totals<<<4, 1024, 0, c->stream>>>(tot, nchunks, nullptr);
+  k_prefix_apply<<<nchunks, 256, 0, c->stream>>>(B.n, c->cap, B.u, B.k, tot, nchunks, B.prefix, nullptr);
+}
 
 void launch_amin2(dzs_ctx* c) {
   c->launches += 1;

@@ -23,14 +23,16 @@
 // search of the keys inside the parent's range.  The numbering depends only
 // on the keys (no atomics), so the tree is deterministic.
 //
-// Bottom-up, in one launch: every leaf sums its particles, then climbs -- the
-// last child to arrive at a parent (atomic counter) sums the children and goes
-// on, the others stop; nothing waits.  Exact integer mass and mass-weighted
-// position (uint64), the rounded integer COM and the largest member
-// multiplicity (node softening).  Walk groups (node with <= G particles whose
-// parent holds more, or a leaf) are listed in Morton order.
-#include <cuda/atomic>
-
+// Node sums in one pass, without a climb: a node's mass and mass-weighted
+// position (uint64, exact) are differences of exclusive prefix sums over the
+// sorted particles at its range ends (a leaf sums its <= B particles
+// directly), giving the rounded integer COM; the largest member
+// multiplicity (node softening) starts at 1 everywhere, and only a leaf
+// holding a merged particle (k > 1) raises its ancestors' value with
+// atomicMax, stopping where an ancestor already holds at least as much (the
+// maximum is order-free, so the tree is deterministic).  Walk groups (node
+// with <= G particles whose parent holds more, or a leaf) are listed in Morton
+// order.
 #include "common.cuh"
 
 namespace dzs {
@@ -171,7 +173,7 @@ __global__ void __launch_bounds__(kTreeTile) k_tree_nodes(
     const int32_t* __restrict__ d_n, int64_t cap, const uint64_t* __restrict__ key, const uint32_t* __restrict__ u,
     const int32_t* __restrict__ info, const int32_t* __restrict__ tcount, int64_t ntiles,
     const int32_t* __restrict__ lvl, const int32_t* __restrict__ cstart, int depth_m, int B, Node* __restrict__ nodes,
-    int32_t* __restrict__ cfirst, int32_t* __restrict__ parent, int32_t* __restrict__ arrive,
+    int32_t* __restrict__ cfirst, int32_t* __restrict__ parent,
     int32_t* __restrict__ groups) {
   __shared__ int32_t wcnt[kTreeTile / 32][kCols];
   __shared__ int32_t base[kCols];
@@ -249,13 +251,12 @@ __global__ void __launch_bounds__(kTreeTile) k_tree_nodes(
     c.cz = (uz & mask) | half;
     c.comx = c.comy = c.comz = 0;
     c.mass = 0;
-    c.kmax = 0;
+    c.kmax = 1;  // every member has k >= 1; raised by the leaves that hold merged particles
     c.start = (int32_t)i;
     c.count = (int32_t)(end - i);
     c.child = j < J ? 0 : -1;  // internal: linked by k_tree_link
     c.meta = (uint32_t)j;
     nodes[rank] = c;
-    if (j < J) arrive[rank] = 0;
     if (j == 0) parent[rank] = -1;
     if (j == g) gnode = rank;
     prev = rank;
@@ -293,12 +294,9 @@ __global__ void k_tree_link(const int32_t* __restrict__ lvl, Node* __restrict__ 
   }
 }
 
-__device__ __forceinline__ void write_node_sums(Node* __restrict__ nodes, uint64_t* __restrict__ nsum,
-                                                int64_t node_cap, int64_t ni, uint64_t K, const uint64_t (&S)[3],
-                                                uint32_t kmax) {
-  for (int ax = 0; ax < 3; ++ax) nsum[ax * node_cap + ni] = S[ax];
+__device__ __forceinline__ void write_mass_com(Node* __restrict__ nodes, int64_t ni, uint64_t K,
+                                               const uint64_t (&S)[3]) {
   nodes[ni].mass = (uint32_t)K;
-  nodes[ni].kmax = kmax;
   if (K > 0) {
     nodes[ni].comx = (uint32_t)((2 * S[0] + K) / (2 * K));
     nodes[ni].comy = (uint32_t)((2 * S[1] + K) / (2 * K));
@@ -306,23 +304,27 @@ __device__ __forceinline__ void write_node_sums(Node* __restrict__ nodes, uint64
   }
 }
 
-// all depths in one launch: leaves sum their particles and climb; at each
-// parent the last child to arrive (after a fence on its writes) sums the
-// children, read from L2 (the writers are other blocks), and climbs on
-__global__ void k_tree_up_all(const int32_t* __restrict__ lvl, int64_t cap, const uint32_t* __restrict__ u,
-                              const uint32_t* __restrict__ k, Node* __restrict__ nodes, uint64_t* __restrict__ nsum,
-                              int64_t node_cap, const int32_t* __restrict__ parent, int32_t* __restrict__ arrive) {
+// every node: leaves sum their particles (four loads in flight at a time) and
+// raise their ancestors' largest multiplicity when it exceeds 1; internal
+// nodes take prefix-sum differences (pre: exclusive [4][cap + 1])
+__global__ void k_tree_sums(const int32_t* __restrict__ lvl, int64_t cap, const uint32_t* __restrict__ u,
+                            const uint32_t* __restrict__ k, const uint64_t* __restrict__ pre,
+                            Node* __restrict__ nodes, const int32_t* __restrict__ parent) {
   int64_t total = 0;
   for (int j = 0; j <= kMaxLevel; ++j) total += lvl[j];
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-    const Node nd = nodes[t];
-    if (nd.child >= 0) continue;  // finished by its last child
+    const int32_t s0 = nodes[t].start, cnt = nodes[t].count, child = nodes[t].child;
     uint64_t K = 0, S[3] = {0, 0, 0};
+    if (child >= 0) {
+      const int64_t e = (int64_t)s0 + cnt;
+      K = pre[e] - pre[s0];
+      for (int ax = 0; ax < 3; ++ax) S[ax] = pre[(int64_t)(1 + ax) * (cap + 1) + e] - pre[(int64_t)(1 + ax) * (cap + 1) + s0];
+      write_mass_com(nodes, t, K, S);
+      continue;
+    }
     uint32_t kmax = 0;
-    // four particles per iteration, their loads issued together (a leaf holds
-    // <= B particles, a depth-21 leaf possibly more)
-    const int64_t i1 = (int64_t)nd.start + nd.count;
-    for (int64_t i0 = nd.start; i0 < i1; i0 += 4) {
+    const int64_t i1 = (int64_t)s0 + cnt;
+    for (int64_t i0 = s0; i0 < i1; i0 += 4) {
       uint32_t kk[4], ux[4], uy[4], uz[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
@@ -342,32 +344,11 @@ __global__ void k_tree_up_all(const int32_t* __restrict__ lvl, int64_t cap, cons
         S[2] += (uint64_t)kk[q] * uz[q];
       }
     }
-    write_node_sums(nodes, nsum, node_cap, t, K, S, kmax);
-    int64_t cur = t;
-    for (;;) {
-      const int32_t par = parent[cur];
-      if (par < 0) break;
-      const int nch = (int)((nodes[par].meta >> 8) & 0xff);
-      // release this subtree's sums with the arrival; the last arriver acquires
-      // every sibling's
-      cuda::atomic_ref<int32_t, cuda::thread_scope_device> arr(arrive[par]);
-      if (arr.fetch_add(1, cuda::memory_order_acq_rel) + 1 < nch) break;
-      const int32_t c0 = nodes[par].child;
-      uint64_t PK = 0, PS[3] = {0, 0, 0};
-      uint32_t pkmax = 0;
-      // the (<= 8) children's sums, all loads issued together
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        if (q < nch) {
-          const int64_t ci = (int64_t)c0 + q;
-          PK += __ldcg(&nodes[ci].mass);
-          pkmax = max(pkmax, __ldcg(&nodes[ci].kmax));
-          for (int ax = 0; ax < 3; ++ax) PS[ax] += __ldcg(&nsum[ax * node_cap + ci]);
-        }
-      }
-      write_node_sums(nodes, nsum, node_cap, par, PK, PS, pkmax);
-      cur = par;
-    }
+    write_mass_com(nodes, t, K, S);
+    nodes[t].kmax = kmax;
+    if (kmax > 1)
+      for (int32_t a = parent[t]; a >= 0; a = parent[a])
+        if (atomicMax(&nodes[a].kmax, kmax) >= kmax) break;  // the rest is raised already (or being raised)
   }
 }
 
@@ -388,11 +369,12 @@ void launch_tree(dzs_ctx* c) {
   k_tree_totals<<<1, 32, 0, c->stream>>>(B.lvl_count, c->node_cap, B.counters, B.err);
   k_tree_nodes<<<(unsigned)ntiles, kTreeTile, 0, c->stream>>>(B.n, c->cap, B.key, B.u, info, tcount, ntiles,
                                                               B.lvl_count, B.cell_start, c->logM, c->P.leaf_bucket,
-                                                              B.nodes, cfirst, B.parent, B.arrive, B.groups);
+                                                              B.nodes, cfirst, B.parent, B.groups);
   k_tree_link<<<grid_for(c->node_cap, kThreads, 8), kThreads, 0, c->stream>>>(B.lvl_count, B.nodes, cfirst,
                                                                                      B.parent);
-  k_tree_up_all<<<grid_for(c->node_cap, kThreads, 8), kThreads, 0, c->stream>>>(
-      B.lvl_count, c->cap, B.u, B.k, B.nodes, B.nsum, c->node_cap, B.parent, B.arrive);
+  launch_mass_prefix(c);
+  k_tree_sums<<<grid_for(c->node_cap, kThreads, 8), kThreads, 0, c->stream>>>(B.lvl_count, c->cap, B.u, B.k,
+                                                                               B.prefix, B.nodes, B.parent);
 }
 
 }  // namespace dzs
