@@ -708,22 +708,31 @@ def measure_e2e(dzs, P, stream, warmup, steps):
             t.numpy().view(arr.dtype)[...] = arr
             pinned[key] = t.numpy().view(arr.dtype)
         h2d = sum(a.nbytes for a in pinned.values())
+        recbuf = torch.empty(n * dzs.RECORD_DTYPE.itemsize, dtype=torch.uint8,
+                             pin_memory=True).numpy().view(dzs.RECORD_DTYPE)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ctx.set_state(pinned, warmup)
+        # pipelined results: step s + 1 is queued before step s's records and
+        # diagnostics are read, so the GPU does not wait for the host
+        ctx.pipeline(True)
         d2h = 0
-        for _ in range(k):
+        if k > 0:
             ctx.step(1)
-            rec = ctx.drain(cap=n)
-            d = ctx.diagnostics()
+        for i in range(1, k + 1):
+            if i < k:
+                ctx.step(1)
+            rec = ctx.drain_step(warmup + i, cap=n, buf=recbuf)
+            d, _ = ctx.step_result(warmup + i)
             d2h += rec.nbytes + d.nbytes
+        ctx.pipeline(False)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
     ctx.close()
     return {"value": P.n1d ** 3 * k / wall, "unit": UNIT, "h2d_bytes_per_step": h2d / max(1, k),
             "d2h_bytes_per_step": d2h / max(1, k), "steps": k, "first_step": warmup,
             "note": "state after the warm-up steps copied in from pinned host memory once; every step's records "
-                    "and diagnostics copied back"}
+                    "and diagnostics copied back (pipelined: step s + 1 runs while step s is read)"}
 
 
 def full_run(dzs, P, stream):
@@ -736,9 +745,13 @@ def full_run(dzs, P, stream):
     nrec = 0
     with torch.cuda.stream(stream):
         ctx.ics()
-        for _ in range(P.nsteps):
-            ctx.step(1)
-            nrec += len(ctx.drain(cap=P.n1d ** 3))
+        ctx.pipeline(True)  # step s + 1 runs while step s's records are drained
+        ctx.step(1)
+        for s in range(1, P.nsteps + 1):
+            if s < P.nsteps:
+                ctx.step(1)
+            nrec += len(ctx.drain_step(s, cap=P.n1d ** 3))
+        ctx.pipeline(False)
         n_end, _ = ctx.count()
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0

@@ -176,6 +176,33 @@ DZS_API dzs_status dzs_run_stages(dzs_ctx* c, uint32_t stage_mask);
  * full (the count of kept records is still valid). */
 DZS_API dzs_status dzs_lightcone_drain(dzs_ctx* c, dzs_lc_record* host_buf, size_t cap, size_t* n_out);
 
+/* Pipelined per-step results (a serving convenience; Sec. 2.1 global steps,
+ * Sec. 2.2 the conserved totals): with on != 0, every step dzs_step runs ends
+ * by enqueueing its conservation diagnostics (as dzs_diagnostics), the
+ * lightcone ring counters and the device error word into pinned host memory
+ * the context owns, behind the step's kernels on the context stream, so that
+ * the caller can read step s while step s + 1 runs.  The last 4 steps are
+ * kept (a step's slot is reused 4 steps later, after its copies landed).
+ * on = 0 waits for the stream and turns it off.  Errors as dzs_step. */
+DZS_API dzs_status dzs_pipeline(dzs_ctx* c, int32_t on);
+
+/* Result of step `step` (the number of steps completed, as dzs_get_count
+ * reports after it): diag[8] as dzs_diagnostics, *lc_written = lightcone
+ * records written up to that step.  Waits only for that step.  Returns
+ * DZS_ESTATE if pipelining is off, DZS_EINVAL if that step's result is not
+ * kept (not run yet, or more than 4 steps ago), DZS_EOVERFLOW if the device
+ * flagged a buffer overflow by then. */
+DZS_API dzs_status dzs_step_result(dzs_ctx* c, int32_t step, double diag[8], uint64_t* lc_written);
+
+/* dzs_lightcone_drain up to the end of step `step` only (a kept step, see
+ * dzs_step_result): the records written since the last drain and up to that
+ * step, at most cap, copied on a copy stream of the context while later steps
+ * keep running; same order, bookkeeping and DZS_EOVERFLOW as
+ * dzs_lightcone_drain.  host_buf is caller-owned (pinned memory copies
+ * fastest). */
+DZS_API dzs_status dzs_lightcone_drain_step(dzs_ctx* c, int32_t step, dzs_lc_record* host_buf, size_t cap,
+                                            size_t* n_out);
+
 /* Free the context and its device memory.  NULL-safe. */
 DZS_API dzs_status dzs_destroy(dzs_ctx* c);
 

@@ -32,7 +32,8 @@ MESH_DELTA, MESH_PHI = 0, 1
 PK_SHOT = 1
 
 EXPORTED = ["dzs_params_default", "dzs_footprint_bytes", "dzs_create", "dzs_ics", "dzs_step",
-            "dzs_run_stages", "dzs_lightcone_drain", "dzs_destroy", "dzs_get_count", "dzs_get_state",
+            "dzs_run_stages", "dzs_lightcone_drain", "dzs_pipeline", "dzs_step_result", "dzs_lightcone_drain_step",
+            "dzs_destroy", "dzs_get_count", "dzs_get_state",
             "dzs_set_state", "dzs_accel", "dzs_merge_only", "dzs_diagnostics", "dzs_get_tables",
             "dzs_get_mesh", "dzs_get_counters", "dzs_get_walk_counters", "dzs_walk_lists", "dzs_measure_fp32_peaks", "dzs_debug_fail_alloc", "dzs_twin_displacement", "dzs_batch_create", "dzs_batch_step",
             "dzs_batch_synchronize", "dzs_batch_destroy", "dzs_set_profiling", "dzs_get_profile",
@@ -116,6 +117,8 @@ def load(path: str = LIB_PATH):
         "dzs_create": [P, vp, C.POINTER(vp)], "dzs_ics": [vp],
         "dzs_step": [vp, i32, C.POINTER(i32)], "dzs_run_stages": [vp, u32],
         "dzs_lightcone_drain": [vp, vp, sz, C.POINTER(sz)], "dzs_destroy": [vp],
+        "dzs_pipeline": [vp, i32], "dzs_step_result": [vp, i32, vp, C.POINTER(C.c_uint64)],
+        "dzs_lightcone_drain_step": [vp, i32, vp, sz, C.POINTER(sz)],
         "dzs_get_count": [vp, C.POINTER(sz), C.POINTER(i32)],
         "dzs_get_state": [vp, vp, vp, vp, vp, vp, vp, sz, C.POINTER(sz)],
         "dzs_set_state": [vp, vp, vp, vp, vp, vp, vp, sz, i32],
@@ -214,6 +217,27 @@ def dzs_lightcone_drain(h, cap: int = 1 << 22, buf=None):
         buf = np.empty(cap, RECORD_DTYPE)
     n = C.c_size_t(0)
     _check(load().dzs_lightcone_drain(h, _ptr(buf), cap, C.byref(n)), h)
+    return buf[:n.value].copy()
+
+
+def dzs_pipeline(h, on: bool = True):
+    _check(load().dzs_pipeline(h, 1 if on else 0), h)
+
+
+def dzs_step_result(h, step: int):
+    """(diagnostics[8], lightcone records written up to that step) of a kept step"""
+    out = np.zeros(8)
+    w = C.c_uint64(0)
+    _check(load().dzs_step_result(h, int(step), _ptr(out), C.byref(w)), h)
+    return out, int(w.value)
+
+
+def dzs_lightcone_drain_step(h, step: int, cap: int = 1 << 22, buf=None):
+    """records of the kept steps up to `step` not yet drained (at most cap)"""
+    if buf is None or len(buf) < cap:
+        buf = np.empty(cap, RECORD_DTYPE)
+    n = C.c_size_t(0)
+    _check(load().dzs_lightcone_drain_step(h, int(step), _ptr(buf), cap, C.byref(n)), h)
     return buf[:n.value].copy()
 
 
@@ -509,6 +533,14 @@ class Context:
         if getattr(self, "_drain_buf", None) is None or len(self._drain_buf) < cap:
             self._drain_buf = np.empty(cap, RECORD_DTYPE)
         return dzs_lightcone_drain(self.h, cap, self._drain_buf)
+    def pipeline(self, on=True): dzs_pipeline(self.h, on)
+    def step_result(self, step): return dzs_step_result(self.h, step)
+    def drain_step(self, step, cap=1 << 22, buf=None):
+        if buf is None:
+            if getattr(self, "_drain_buf", None) is None or len(self._drain_buf) < cap:
+                self._drain_buf = np.empty(cap, RECORD_DTYPE)
+            buf = self._drain_buf
+        return dzs_lightcone_drain_step(self.h, step, cap, buf)
     def state(self): return dzs_get_state(self.h)
     def set_state(self, st, step, with_g=True): dzs_set_state(self.h, st, step, with_g)
     def accel(self, parts=ACC_ALL): return dzs_accel(self.h, parts)

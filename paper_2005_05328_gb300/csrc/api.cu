@@ -454,6 +454,13 @@ dzs_status dzs_destroy(dzs_ctx* c) {
     cudaEventDestroy(pe.b);
   }
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  for (cudaEvent_t e : c->pipe_ev)
+    if (e) cudaEventDestroy(e);
+  if (c->pipe) cudaFreeHost(c->pipe);
+  if (c->copy_stream) {
+    cudaStreamSynchronize(c->copy_stream);
+    cudaStreamDestroy(c->copy_stream);
+  }
   if (c->arena) cudaFree(c->arena);
   if (c->obs.sky) cudaFree(c->obs.sky);
   if (c->obs.grid) cudaFree(c->obs.grid);
@@ -551,6 +558,23 @@ dzs_status ring_guard(dzs_ctx* c) {
   return DZS_OK;
 }
 
+// end of a step in pipelined mode: its diagnostics, ring counters and error
+// word copied to the step's pinned slot behind the step's kernels; the slot of
+// the step kPipe earlier is reused once its copies have landed
+dzs_status pipe_record(dzs_ctx* c) {
+  const int32_t s = c->step;
+  const int k = s % dzs_ctx::kPipe;
+  CK(cudaEventSynchronize(c->pipe_ev[k]));
+  launch_diagnostics(c);
+  dzs_ctx::PipeSlot* slot = c->pipe + k;
+  CK(cudaMemcpyAsync(slot->diag, c->B.diag, sizeof slot->diag, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(slot->ring, c->B.counters, sizeof slot->ring, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(slot->err, c->B.err, sizeof slot->err, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaEventRecord(c->pipe_ev[k], c->stream));
+  c->pipe_step[k] = s;
+  return DZS_OK;
+}
+
 dzs_status dzs_step(dzs_ctx* c, int32_t nsteps, int32_t* steps_done) {
   dzs_status s = guard(c);
   if (s) return s;
@@ -560,6 +584,7 @@ dzs_status dzs_step(dzs_ctx* c, int32_t nsteps, int32_t* steps_done) {
   while (done < nsteps && c->step < c->P.nsteps) {
     s = ring_guard(c);
     if (!s) s = dzs_run_stages(c, DZS_STAGE_ALL);
+    if (!s && c->pipe_on) s = pipe_record(c);
     if (s) {
       if (steps_done) *steps_done = done;
       return s;
@@ -637,6 +662,83 @@ dzs_status dzs_lightcone_drain(dzs_ctx* c, dzs_lc_record* host_buf, size_t cap, 
   if (ctr[1]) {
     char buf[128];
     snprintf(buf, sizeof buf, "%llu lightcone records dropped (ring full)", (unsigned long long)ctr[1]);
+    return fail(c, DZS_EOVERFLOW, buf);
+  }
+  return DZS_OK;
+}
+
+dzs_status dzs_pipeline(dzs_ctx* c, int32_t on) {
+  dzs_status s = guard(c);
+  if (s) return s;
+  if (on && !c->pipe) {
+    CK(cudaHostAlloc((void**)&c->pipe, sizeof(dzs_ctx::PipeSlot) * dzs_ctx::kPipe, cudaHostAllocDefault));
+    for (int k = 0; k < dzs_ctx::kPipe; ++k) CK(cudaEventCreateWithFlags(&c->pipe_ev[k], cudaEventDisableTiming));
+    CK(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+  }
+  if (!on) CK(cudaStreamSynchronize(c->stream));
+  for (int k = 0; k < dzs_ctx::kPipe; ++k) c->pipe_step[k] = -1;
+  c->pipe_on = on != 0;
+  return DZS_OK;
+}
+
+namespace {
+// the pinned slot holding completed-step count `step`, after its copies landed
+dzs_status pipe_slot(dzs_ctx* c, int32_t step, const dzs_ctx::PipeSlot** out) {
+  if (!c->pipe_on) return fail(c, DZS_ESTATE, "pipelined results are off (dzs_pipeline)");
+  const int k = ((step % dzs_ctx::kPipe) + dzs_ctx::kPipe) % dzs_ctx::kPipe;
+  if (step < 0 || c->pipe_step[k] != step)
+    return fail(c, DZS_EINVAL, "no result kept for that step (only the last 4 steps are)");
+  CK(cudaEventSynchronize(c->pipe_ev[k]));
+  const dzs_ctx::PipeSlot* slot = c->pipe + k;
+  if (slot->err[0] & (kErrNodes | kErrStack | kErrGroups)) {
+    char buf[160];
+    snprintf(buf, sizeof buf, "device buffer overflow (error word 0x%x)", slot->err[0]);
+    return fail(c, DZS_EOVERFLOW, buf);
+  }
+  *out = slot;
+  return DZS_OK;
+}
+}  // namespace
+
+dzs_status dzs_step_result(dzs_ctx* c, int32_t step, double diag[8], uint64_t* lc_written) {
+  dzs_status s = guard(c);
+  if (s) return s;
+  const dzs_ctx::PipeSlot* slot = nullptr;
+  s = pipe_slot(c, step, &slot);
+  if (s) return s;
+  if (diag) std::memcpy(diag, slot->diag, sizeof slot->diag);
+  if (lc_written) *lc_written = slot->ring[0];
+  return DZS_OK;
+}
+
+dzs_status dzs_lightcone_drain_step(dzs_ctx* c, int32_t step, dzs_lc_record* host_buf, size_t cap, size_t* n_out) {
+  dzs_status s = guard(c);
+  if (s) return s;
+  if (n_out) *n_out = 0;
+  if (!host_buf && cap) return fail(c, DZS_EINVAL, "host_buf is NULL");
+  const dzs_ctx::PipeSlot* slot = nullptr;
+  s = pipe_slot(c, step, &slot);
+  if (s) return s;
+  // records [drained, head of that step) are complete and stay in place while
+  // later steps append: copied on the copy stream beside the running kernels
+  const uint64_t head = slot->ring[0];
+  const uint64_t avail = head > c->drained ? head - c->drained : 0;
+  const uint64_t take = avail < cap ? avail : cap;
+  uint64_t done = 0;
+  while (done < take) {
+    const uint64_t ring_slot = (c->drained + done) % c->ring_cap;
+    uint64_t chunk = c->ring_cap - ring_slot;
+    if (chunk > take - done) chunk = take - done;
+    CK(cudaMemcpyAsync(host_buf + done, c->B.ring + ring_slot, chunk * sizeof(dzs_lc_record), cudaMemcpyDeviceToHost,
+                       c->copy_stream));
+    done += chunk;
+  }
+  CK(cudaStreamSynchronize(c->copy_stream));
+  c->drained += take;
+  if (n_out) *n_out = (size_t)take;
+  if (slot->ring[1]) {
+    char buf[128];
+    snprintf(buf, sizeof buf, "%llu lightcone records dropped (ring full)", (unsigned long long)slot->ring[1]);
     return fail(c, DZS_EOVERFLOW, buf);
   }
   return DZS_OK;

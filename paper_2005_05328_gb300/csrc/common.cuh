@@ -203,6 +203,20 @@ struct dzs_ctx {
   std::vector<cudaEvent_t> ev_pool;
   double prof_ms[8] = {0};
   uint64_t prof_calls[8] = {0};
+  // pipelined per-step results (dzs_pipeline): the last kPipe steps' diagnostics,
+  // ring head, dropped count and error word in pinned host memory, each slot
+  // written by copies enqueued at the end of its step and closed by an event
+  static constexpr int kPipe = 4;
+  struct PipeSlot {
+    double diag[8];
+    uint64_t ring[2];  // records written so far, dropped so far
+    uint32_t err[4];
+  };
+  bool pipe_on = false;
+  PipeSlot* pipe = nullptr;  // [kPipe], pinned
+  cudaEvent_t pipe_ev[kPipe] = {nullptr, nullptr, nullptr, nullptr};
+  int32_t pipe_step[kPipe] = {-1, -1, -1, -1};  // completed-step count each slot holds
+  cudaStream_t copy_stream = nullptr;          // record copies beside the compute stream
 };
 
 namespace dzs {
