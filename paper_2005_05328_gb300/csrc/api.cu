@@ -88,7 +88,7 @@ struct Plan {
   int64_t cap, node_cap, m3, nspec, nb, nchunks, ring;
   size_t rsz;
   size_t o_u, o_u2, o_p, o_p2, o_g, o_gsave, o_k, o_k2, o_id, o_id2, o_fl, o_fl2, o_key, o_key2, o_idx, o_idx2, o_hist,
-      o_blocksum, o_iscan, o_prefix, o_mend, o_nodes, o_lvl, o_nsum, o_parent, o_arrive, o_cicw, o_groups, o_ghead, o_wpm, o_wph, o_wnh, o_wlen,
+      o_blocksum, o_iscan, o_prefix, o_mend, o_nodes, o_lvl, o_cfirst, o_parent, o_cicw, o_groups, o_ghead, o_wpm, o_wph, o_wnh, o_wlen,
       o_rho, o_spec, o_phi,
       o_cstart, o_tw, o_green, o_ring, o_n, o_err, o_counters, o_diag, o_convert;
   size_t total;
@@ -125,9 +125,8 @@ struct Plan {
     o_mend = L.take(4 * cap);
     o_nodes = L.take(sizeof(Node) * node_cap);
     o_lvl = L.take(4 * 32);
-    o_nsum = L.take(8 * 3 * node_cap);
+    o_cfirst = L.take(4 * node_cap);
     o_parent = L.take(4 * node_cap);
-    o_arrive = L.take(4 * node_cap);
     o_cicw = L.take(8 * rsz * cap);
     o_groups = L.take(4 * cap);
     o_ghead = L.take(4 * cap);
@@ -406,9 +405,8 @@ dzs_status dzs_create(const dzs_params* p, void* cuda_stream, dzs_ctx** out) {
   B.mend = (int32_t*)(a + pl.o_mend);
   B.nodes = (Node*)(a + pl.o_nodes);
   B.lvl_count = (int32_t*)(a + pl.o_lvl);
-  B.nsum = (uint64_t*)(a + pl.o_nsum);
+  B.cfirst = (int32_t*)(a + pl.o_cfirst);
   B.parent = (int32_t*)(a + pl.o_parent);
-  B.arrive = (int32_t*)(a + pl.o_arrive);
   B.cicw = a + pl.o_cicw;
   B.groups = (int32_t*)(a + pl.o_groups);
   B.group_head = (int32_t*)(a + pl.o_ghead);

@@ -115,9 +115,8 @@ struct Buffers {
   // tree
   Node* nodes = nullptr;
   int32_t* lvl_count = nullptr;  // [kMaxLevel + 2]
-  uint64_t* nsum = nullptr;      // [3][node cap] scratch sums
+  int32_t* cfirst = nullptr;     // [node cap] first-child index of each node (tree build)
   int32_t* parent = nullptr;     // [node cap] parent node (-1 at the root)
-  int32_t* arrive = nullptr;     // [node cap] children finished (bottom-up pass)
   void* cicw = nullptr;          // real [8][cap] CIC corner weight sums per mesh cell (deposit)
   int32_t* groups = nullptr;     // [cap]
   void* wpm = nullptr;           // real [cap]: G m / s^2 per particle (walk, lattice units)

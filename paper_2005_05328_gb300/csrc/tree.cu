@@ -362,7 +362,7 @@ void launch_tree(dzs_ctx* c) {
   const int64_t ntiles = (c->cap + kTreeTile - 1) / kTreeTile;
   int32_t* info = B.group_head;       // [cap] per-particle L, J, g
   int32_t* tcount = B.iscan;          // [kCols][ntiles] tile counts, then offsets
-  int32_t* cfirst = (int32_t*)B.nsum; // [node_cap] (the sums are written after)
+  int32_t* cfirst = B.cfirst;         // [node_cap]
   k_tree_count<<<(unsigned)ntiles, kTreeTile, 0, c->stream>>>(B.n, B.key, c->P.leaf_bucket, c->P.walk_group, info,
                                                               tcount, ntiles);
   k_tree_scan<<<kCols, 1024, 0, c->stream>>>(tcount, ntiles, B.lvl_count);
