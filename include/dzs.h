@@ -435,15 +435,16 @@ DZS_API dzs_status dzs_get_mesh(dzs_ctx* c, int32_t which, double* out);
  * [2] pair evaluations (interaction-list entries x group particles) summed
  * since the last dzs_ics / dzs_set_state / dzs_set_profiling, [3] device error
  * word, [4] kernels launched by this context so far, [5] lightcone records
-  * written so far, [6] deepest tree-walk stack use (entries, of 1024),
- * [7] tree-walk node tests and [8] traversal rounds summed like [2]. */
+  * written so far, [6] deepest tree-walk stack use (entries, of 512),
+ * [7] tree-walk node tests and [8] traversal rounds summed like [2] ([6]-[8]
+ * counted only with DZS_PROFILE_WALK, see dzs_set_profiling). */
 DZS_API dzs_status dzs_get_counters(dzs_ctx* c, uint64_t out[9]);
 
 /* Tree-walk work counters (Sec. 2.1 short-range force), summed like
  * dzs_get_counters' [2]: [0] listed pairs (interaction-list entries x group
  * particles, the same count as dzs_get_counters [2]), [1] pairs evaluated in
  * range (0 < r < r_cut: the pairs that carry force), [2] node tests, [3]
- * traversal rounds, [4] group walks started from the window of deep frontier
+ * traversal rounds ([2] and [3] with DZS_PROFILE_WALK only), [4] group walks started from the window of deep frontier
  * cells around the group, [5] group walks that fell back to the shallow
  * frontier (a node between the two frontier depths might have been accepted).
  * Synchronises the context stream. */
@@ -472,9 +473,14 @@ enum {
   DZS_PROF_N = 7
 };
 
-/* Enable (1) or disable (0) per-stage CUDA-event timing on the context
- * stream and reset the accumulators and the pair counter.  Timing adds two
- * event records per stage and no synchronisation. */
+/* Profiling flags: DZS_PROFILE_STAGES (= 1) per-stage CUDA-event timing on
+ * the context stream (two event records per stage, no synchronisation);
+ * DZS_PROFILE_WALK (= 2) the tree walk's node-test, traversal-round and
+ * deepest-stack counters (dzs_get_walk_counters [2] and [3],
+ * dzs_get_counters [6]-[8]; 0 while off: counting costs ~1.5% of the
+ * walk).  Any call resets the accumulators and the pair counters.  The pair
+ * counts themselves (listed and in range) are always kept. */
+enum { DZS_PROFILE_STAGES = 1, DZS_PROFILE_WALK = 2 };
 DZS_API dzs_status dzs_set_profiling(dzs_ctx* c, int32_t enable);
 
 /* Device milliseconds and call counts per category since the last

@@ -295,8 +295,13 @@ def dzs_get_mesh(h, which: int, mesh: int):
     return out.reshape(mesh, mesh, mesh)
 
 
-def dzs_set_profiling(h, enable: bool):
-    _check(load().dzs_set_profiling(h, 1 if enable else 0), h)
+PROFILE_STAGES, PROFILE_WALK = 1, 2
+
+
+def dzs_set_profiling(h, enable: bool, walk_diag: bool = False):
+    """stage timers on/off; walk_diag: also count the walk's node tests,
+    rounds and deepest stack use"""
+    _check(load().dzs_set_profiling(h, (PROFILE_STAGES if enable else 0) | (PROFILE_WALK if walk_diag else 0)), h)
 
 
 def dzs_get_profile(h):
@@ -551,7 +556,7 @@ class Context:
     def counters(self): return dzs_get_counters(self.h)
     def walk_counters(self): return dzs_get_walk_counters(self.h)
     def walk_lists(self): return dzs_walk_lists(self.h)
-    def set_profiling(self, on=True): dzs_set_profiling(self.h, on)
+    def set_profiling(self, on=True, walk_diag=False): dzs_set_profiling(self.h, on, walk_diag)
     def profile(self): return dzs_get_profile(self.h)
     def checkpoint(self): return dzs_checkpoint(self.h)
     def restore(self, blob): dzs_restore(self.h, blob)

@@ -1224,7 +1224,8 @@ dzs_status dzs_set_profiling(dzs_ctx* c, int32_t enable) {
   CK(cudaMemsetAsync(c->B.counters + 4, 0, 4 * sizeof(uint64_t), c->stream));
   CK(cudaMemsetAsync(c->B.counters + 12, 0, 2 * sizeof(uint64_t), c->stream));
   CK(cudaMemsetAsync(c->B.counters + 20, 0, 2 * sizeof(uint64_t), c->stream));
-  c->prof_on = enable != 0;
+  c->prof_on = (enable & DZS_PROFILE_STAGES) != 0;
+  c->walk_diag = (enable & DZS_PROFILE_WALK) != 0;
   return DZS_OK;
 }
 

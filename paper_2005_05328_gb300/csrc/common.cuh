@@ -194,6 +194,7 @@ struct dzs_ctx {
   uint64_t launches = 0;  // kernels launched (host-side count)
   // per-stage CUDA-event profiling
   bool prof_on = false;
+  bool walk_diag = false;  // count the walk's node tests, rounds and stack depth
   struct ProfEv {
     int cat;
     cudaEvent_t a, b;

@@ -522,8 +522,10 @@ __global__ void k_front_fill_F(const int32_t* __restrict__ lvl, const Node* __re
 
 // kMasked: evaluate lists with the range-masked pass (pays off when many
 // listed entries lie beyond r_cut of a given particle: groups not small
-// against r_cut), else with one range-guarded pass
-template <class R, bool kMasked>
+// against r_cut), else with one range-guarded pass.  kDiag: also count node
+// tests, traversal rounds and the deepest stack use (three instructions per
+// round, ~1.5% of the walk: only while asked for)
+template <class R, bool kMasked, bool kDiag>
 __global__ void __launch_bounds__(kWarps * 32, sizeof(R) == 4 ? 8 : 5) k_walk(
     const int32_t* __restrict__ groups, const uint64_t* __restrict__ counters, unsigned int* __restrict__ next,
     const Node* __restrict__ nodes, const R* __restrict__ nh, int64_t cap, const uint32_t* __restrict__ u,
@@ -648,8 +650,10 @@ __global__ void __launch_bounds__(kWarps * 32, sizeof(R) == 4 ? 8 : 5) k_walk(
           // most 32 monopoles and the leaves that fit; the others wait)
           if (len > kList - 64) DZS_WALK_FLUSH();
           const int npop = top < 32 ? top : 32;
-          ntests += npop;
-          nrounds += 1;
+          if (kDiag) {
+            ntests += npop;
+            nrounds += 1;
+          }
           int ni = lane < npop ? sm.stack[w][top - npop + lane] : -1;
           top -= npop;
           __syncwarp();
@@ -736,7 +740,7 @@ __global__ void __launch_bounds__(kWarps * 32, sizeof(R) == 4 ? 8 : 5) k_walk(
           for (int q = 0; q < 8; ++q)
             if (q < nch) sm.stack[w][top + ex + q] = nd.child + q;
           top += tot;
-          maxtop = top > maxtop ? top : maxtop;
+          if (kDiag) maxtop = top > maxtop ? top : maxtop;
           // particles of opened small leaves, copied cooperatively (item t of
           // the round belongs to the lane whose inclusive end first exceeds t);
           // a particle farther than r_cut from the group cube acts on none of
@@ -851,9 +855,11 @@ __global__ void __launch_bounds__(kWarps * 32, sizeof(R) == 4 ? 8 : 5) k_walk(
   for (int o = 16; o > 0; o >>= 1) nin64 += __shfl_down_sync(0xffffffffu, nin64, o);
   if (lane == 0 && npairs) atomicAdd(pairs, (unsigned long long)npairs);
   if (lane == 0 && nin64) atomicAdd(pairs + 1, nin64);
-  if (lane == 0) atomicMax(pairs + 3, (unsigned long long)maxtop);
-  if (lane == 0) atomicAdd(pairs + 8, (unsigned long long)ntests);
-  if (lane == 0) atomicAdd(pairs + 9, (unsigned long long)nrounds);
+  if (kDiag && lane == 0) {
+    atomicMax(pairs + 3, (unsigned long long)maxtop);
+    atomicAdd(pairs + 8, (unsigned long long)ntests);
+    atomicAdd(pairs + 9, (unsigned long long)nrounds);
+  }
   if (lane == 0 && nwin) atomicAdd(pairs + 16, (unsigned long long)nwin);
   if (lane == 0 && nfall) atomicAdd(pairs + 17, (unsigned long long)nfall);
 }
@@ -967,12 +973,14 @@ void walk_impl(dzs_ctx* c, bool tree, bool close_kick, int step) {
   const double spacing = c->P.box / c->P.n1d;
   const bool masked = c->P.walk_eval == DZS_WALK_MASKED ||
                       (c->P.walk_eval == DZS_WALK_AUTO && 4.0 * spacing >= c->rcut);
-  auto kern = masked ? k_walk<R, true> : k_walk<R, false>;
+  const bool diag = c->walk_diag;
+  auto kern = masked ? (diag ? k_walk<R, true, true> : k_walk<R, true, false>)
+                     : (diag ? k_walk<R, false, true> : k_walk<R, false, false>);
   size_t sm = sizeof(WalkSmem<R>);
-  static bool attr_done[2][2] = {{false, false}, {false, false}};
-  if (!attr_done[sizeof(R) == 8][masked]) {
+  static bool attr_done[2][2][2] = {};
+  if (!attr_done[sizeof(R) == 8][masked][diag]) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    attr_done[sizeof(R) == 8][masked] = true;
+    attr_done[sizeof(R) == 8][masked][diag] = true;
   }
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWarps * 32, sm);

@@ -77,3 +77,21 @@ def test_window_frontier_builds_the_root_walk_sets(dzs, name):
         else:
             assert np.percentile(rel, 99.9) <= 1e-4, (name, np.percentile(rel, 99.9))
         print(name, "precision", precision, "window", int(wc[4]), "fallback", int(wc[5]))
+
+
+def test_walk_diagnostics_are_opt_in(dzs):
+    """node tests, rounds and stack depth are counted only with the walk
+    diagnostics flag; the accelerations do not depend on it"""
+    kw, z, multi = CASES["32cubed_z0.3"]
+    P, st = sorted_state(kw, z, multi)
+    out = {}
+    for diag in (False, True):
+        with dzs.Context(**kw, z_init=z, precision=0) as ctx:
+            ctx.set_state(st, 0)
+            ctx.set_profiling(True, walk_diag=diag)
+            g = ctx.accel()
+            out[diag] = (g, ctx.walk_counters(), ctx.counters())
+    assert np.array_equal(out[False][0], out[True][0])
+    assert out[False][1][2] == 0 and out[False][1][3] == 0 and out[False][2][6] == 0
+    assert out[True][1][2] > 0 and out[True][1][3] > 0 and out[True][2][6] > 0
+    assert np.array_equal(out[False][1][[0, 1, 4, 5]], out[True][1][[0, 1, 4, 5]])
