@@ -72,8 +72,8 @@ IMPL_BYTES = {
 # of the bench mock, profiles/ncu_k_walk_c2_128cubed_step11.md) and the walk
 # source it was taken on: reported as roofline traffic only while the source
 # is unchanged
-WALK_TRAFFIC_BYTES = 174.592256e6 + 38.467840e6
-WALK_TRAFFIC_SRC = "278b65b2a73da517"
+WALK_TRAFFIC_BYTES = 174.898944e6 + 37.743104e6
+WALK_TRAFFIC_SRC = "393e708687aa1c7f"
 
 # serving sample (Poisson stream of mock requests, sizes 32^3 .. 256^3)
 SERVE_RATE = 4.0
