@@ -367,8 +367,8 @@ typedef struct {
   dzs_params base;         /* everything but n1d, mesh, box, sigma8, seed (capacity ignored) */
 } dzs_serve_config;
 
-/* Batches (SURVEY's batching API for the batched and serving configurations;
- * the paper has one simulation per run): a batch steps several contexts
+/* Batches (for many independent mocks on one GPU, batched or served; the
+ * paper has one simulation per run): a batch steps several contexts
  * together.  dzs_batch_create keeps the n context pointers (it does not own
  * the contexts; they must outlive the batch) and uses host_threads worker
  * threads (0: min(8, hardware threads)).  dzs_batch_step enqueues up to
