@@ -73,7 +73,7 @@ IMPL_BYTES = {
 # source it was taken on: reported as roofline traffic only while the source
 # is unchanged
 WALK_TRAFFIC_BYTES = 174.898944e6 + 37.743104e6
-WALK_TRAFFIC_SRC = "393e708687aa1c7f"
+WALK_TRAFFIC_SRC = "0c63137890d7c797"
 
 # serving sample (Poisson stream of mock requests, sizes 32^3 .. 256^3)
 SERVE_RATE = 4.0

@@ -55,7 +55,7 @@ namespace dzs {
 namespace {
 
 // shared memory sets the occupancy (8 blocks of 4 warps per SM in FP32, 64
-// registers): stack 512 entries (deepest use measured 308; an overflow sets an
+// registers): stack 512 entries (deepest use measured 329; an overflow sets an
 // error bit), list 236 entries (8 blocks measured 2% faster than 7 blocks
 // with 300-entry lists)
 constexpr int kWarps = 4;
